@@ -1,0 +1,458 @@
+/*
+ * ssm_oracle.c -- plain FP64 CPU oracle of the split-step method (SSM) for
+ * McKean-Vlasov SDEs of Chen & dos Reis, "A flexible split-step scheme for
+ * solving McKean-Vlasov stochastic differential equations" (arXiv:2105.09688).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the CUDA path is checked against.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * What it computes (all in IEEE double, no fused multiply-add, sums over
+ * particles in index order):
+ *
+ *   Interacting particle system, §1 Eq. (MV-SDE Propagation): N particles in
+ *   R^d, empirical measure mu^N = (1/N) sum_{j=1..N} delta_{X^j} (self term
+ *   included, weight 1/N).
+ *
+ *   SSM, §2.3 (eq. SSTM:scheme 1 and SSTM:scheme 2), uniform grid t_n = n h:
+ *     step 1 (implicit):  Y_i = X_i + h v(t_n, Y_i, mu^X_n)      (mu^X frozen)
+ *     step 2 (explicit):  X'_i = Y_i + h b(t_n, Y_i, mu^Y_n)
+ *                                    + sigma(t_n, Y_i, mu^Y_n) dW_i
+ *   with dW_i ~ N(0, h I_d) drawn from Philox4x32-10 (below).
+ *
+ * Coefficient sets (the paper leaves the workloads' coefficients to the user;
+ * these are the ones the hot path is built for):
+ *   ORC_COEF_CUBIC1D_GAUSS, d = 1:
+ *     v(x) = x - x^3,  b(y, mu) = 0.5 * int (z - y) exp(-(y - z)^2) mu(dz),
+ *     sigma(y) = 0.4 y + 0.1.
+ *   ORC_COEF_COUPLED3D, d = 3:
+ *     v(y, mu) = -y|y|^2 + 0.5 * int (z - y) / (1 + |y - z|^2) mu(dz),
+ *     b(y, mu) = int (z - y) exp(-|y - z|^2 / 2) mu(dz),
+ *     sigma(y) = diag(0.3 y_k + 0.2).
+ *   ORC_COEF_OU, any d (componentwise), §3.4.1 Eq. (stablity:OU):
+ *     v(x) = rho x,  b(mu) = lambda * int z mu(dz),  sigma = eta.
+ *
+ * The implicit step is solved as follows.
+ *   CUBIC1D_GAUSS: h y^3 + (1 - h) y - x = 0 has exactly one real root for
+ *     0 < h < 1 (Lemma 4.1 with L_v = 1).  Cardano's formula in a
+ *     cancellation-free form, then one Newton correction.
+ *   COUPLED3D: Newton's method on F(y) = y - x - h v(y, mu^X) with the exact
+ *     3x3 Jacobian, Gaussian elimination with partial pivoting, step halving
+ *     when the residual grows, start y = x.
+ *   OU: y = x / (1 - h rho) (Remark 4.3 gives this closed form for v = a x).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11), key = (seed mod 2^32, seed >> 32),
+ * counter = (particle i, step index, stream, call k).  Each FP64 uniform is
+ * u = (k53 + 1) 2^-53 in (0, 1], with k53 the top 53 bits of (w_a << 32 | w_b).
+ * Normals by Box-Muller: r = sqrt(-2 ln u1), z0 = r cos(2 pi u2),
+ * z1 = r sin(2 pi u2).  d = 1 uses z0 of call 0; d = 3 uses z0, z1 of call 0
+ * and z0 of call 1.  Stream 0 draws X_0, stream 1 draws the Brownian
+ * increments.  With fine_log2 = L > 0 the Brownian path lives on the grid
+ * T 2^-L and a coarse increment is the sum of its fine increments, so runs at
+ * different h share one path (§3: every method uses the same Brownian paths).
+ */
+#include "ssm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10                                                             */
+/* ------------------------------------------------------------------------ */
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    /* Multipliers and Weyl key increments of the Philox-4x32 family (SC'11, Table 2). */
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(M0, c0, &hi0, &lo0);
+        mulhilo32(M1, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double uniform53(uint32_t a, uint32_t b)
+{
+    uint64_t w = ((uint64_t)a << 32) | (uint64_t)b;
+    uint64_t k = w >> 11;                       /* 53 bits */
+    return (double)(k + 1) * (1.0 / 9007199254740992.0); /* 2^-53, u in (0, 1] */
+}
+
+/* Two standard normals from one Philox call at counter (i, step, stream, k). */
+static void box_muller_pair(uint64_t seed, uint32_t i, uint32_t step, uint32_t stream,
+                            uint32_t k, double *z0, double *z1)
+{
+    uint32_t ctr[4] = { i, step, stream, k };
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double u1 = uniform53(w[0], w[1]);
+    double u2 = uniform53(w[2], w[3]);
+    double r = sqrt(-2.0 * log(u1));
+    double a = 2.0 * ORC_PI * u2;
+    *z0 = r * cos(a);
+    *z1 = r * sin(a);
+}
+
+void orc_normals(uint64_t seed, int d, int64_t i, int64_t step, int stream, double *z)
+{
+    double a, b;
+    box_muller_pair(seed, (uint32_t)i, (uint32_t)step, (uint32_t)stream, 0u, &a, &b);
+    z[0] = a;
+    if (d == 1) return;
+    z[1] = b;
+    box_muller_pair(seed, (uint32_t)i, (uint32_t)step, (uint32_t)stream, 1u, &a, &b);
+    z[2] = a;
+}
+
+/* Brownian increment dW_n^i (d components) on the step's own grid or as a sum of
+ * fine increments of the grid T 2^-fine_log2. */
+void orc_brownian(const orc_problem *P, int64_t i, int64_t n, double *dw)
+{
+    const int d = P->d;
+    double z[3];
+    for (int c = 0; c < d; ++c) dw[c] = 0.0;
+    if (P->fine_log2 <= 0) {
+        orc_normals(P->seed, d, i, n, 1, z);
+        double sh = sqrt(P->h);
+        for (int c = 0; c < d; ++c) dw[c] = sh * z[c];
+        return;
+    }
+    /* r fine steps of length hf per coarse step; requires h = r * hf exactly. */
+    double hf = P->T / (double)((int64_t)1 << P->fine_log2);
+    int64_t r = (int64_t)llround(P->h / hf);
+    double shf = sqrt(hf);
+    for (int64_t m = 0; m < r; ++m) {
+        orc_normals(P->seed, d, i, n * r + m, 1, z);
+        for (int c = 0; c < d; ++c) dw[c] += shf * z[c];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* b(y_i, mu^Y) for the pairwise sets; y is the particle-major array of all
+ * particles (the support of the empirical measure). */
+static void drift_b(const orc_problem *P, const double *y, const double *yi, double *b)
+{
+    const int d = P->d;
+    const int64_t N = P->N;
+    if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
+        double s = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double dz = y[j] - yi[0];
+            s += dz * exp(-(dz * dz));
+        }
+        b[0] = 0.5 * (s / (double)N);
+    } else if (P->coef == ORC_COEF_COUPLED3D) {
+        double s[3] = { 0.0, 0.0, 0.0 };
+        for (int64_t j = 0; j < N; ++j) {
+            double d0 = y[3 * j + 0] - yi[0];
+            double d1 = y[3 * j + 1] - yi[1];
+            double d2 = y[3 * j + 2] - yi[2];
+            double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            double e = exp(-r2 / 2.0);
+            s[0] += d0 * e; s[1] += d1 * e; s[2] += d2 * e;
+        }
+        for (int c = 0; c < 3; ++c) b[c] = s[c] / (double)N;
+    } else { /* OU: lambda * mean */
+        for (int c = 0; c < d; ++c) {
+            double s = 0.0;
+            for (int64_t j = 0; j < N; ++j) s += y[d * j + c];
+            b[c] = P->p[1] * (s / (double)N);
+        }
+    }
+}
+
+static void diffusion_times_dw(const orc_problem *P, const double *yi, const double *dw, double *out)
+{
+    const int d = P->d;
+    if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
+        out[0] = (0.4 * yi[0] + 0.1) * dw[0];
+    } else if (P->coef == ORC_COEF_COUPLED3D) {
+        for (int c = 0; c < 3; ++c) out[c] = (0.3 * yi[c] + 0.2) * dw[c];
+    } else {
+        for (int c = 0; c < d; ++c) out[c] = P->p[2] * dw[c];
+    }
+}
+
+/* Pair part of v for COUPLED3D at the point y against mu^X:
+ *   S(y)  = (1/N) sum_j (x_j - y) w_j,  w_j = 1 / (1 + |x_j - y|^2)
+ *   JS(y) = dS/dy = (1/N) sum_j ( -w_j I + 2 w_j^2 (x_j - y)(x_j - y)^T ). */
+static void pair_sum_coupled(const orc_problem *P, const double *x, const double *y,
+                             double S[3], double JS[9])
+{
+    const int64_t N = P->N;
+    double s[3] = { 0, 0, 0 };
+    double j9[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
+    for (int64_t j = 0; j < N; ++j) {
+        double dd[3] = { x[3 * j] - y[0], x[3 * j + 1] - y[1], x[3 * j + 2] - y[2] };
+        double w = 1.0 / (1.0 + dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        for (int a = 0; a < 3; ++a) {
+            s[a] += dd[a] * w;
+            for (int c = 0; c < 3; ++c)
+                j9[3 * a + c] += (a == c ? -w : 0.0) + 2.0 * w * w * dd[a] * dd[c];
+        }
+    }
+    for (int a = 0; a < 3; ++a) S[a] = s[a] / (double)N;
+    if (JS)
+        for (int k = 0; k < 9; ++k) JS[k] = j9[k] / (double)N;
+}
+
+/* Residual F(y) = y - x_i - h v(y, mu^X) for COUPLED3D, and optionally its Jacobian. */
+static void coupled_residual(const orc_problem *P, const double *x, const double *xi,
+                             const double *y, double F[3], double J[9])
+{
+    double S[3], JS[9];
+    pair_sum_coupled(P, x, y, S, J ? JS : NULL);
+    double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    for (int a = 0; a < 3; ++a) {
+        double v = -y[a] * r2 + 0.5 * S[a];
+        F[a] = y[a] - xi[a] - P->h * v;
+    }
+    if (J) {
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                /* dv_a/dy_c = -(r2 delta_ac + 2 y_a y_c) + 0.5 JS_ac */
+                double dv = -((a == c ? r2 : 0.0) + 2.0 * y[a] * y[c]) + 0.5 * JS[3 * a + c];
+                J[3 * a + c] = (a == c ? 1.0 : 0.0) - P->h * dv;
+            }
+    }
+}
+
+/* Solve the 3x3 system A s = r by Gaussian elimination with partial pivoting. */
+static int solve3(const double A_in[9], const double r_in[3], double s[3])
+{
+    double A[3][4];
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < 3; ++c) A[a][c] = A_in[3 * a + c];
+        A[a][3] = r_in[a];
+    }
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int row = col + 1; row < 3; ++row)
+            if (fabs(A[row][col]) > fabs(A[piv][col])) piv = row;
+        if (A[piv][col] == 0.0) return -1;
+        if (piv != col)
+            for (int c = 0; c < 4; ++c) { double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t; }
+        for (int row = col + 1; row < 3; ++row) {
+            double f = A[row][col] / A[col][col];
+            for (int c = col; c < 4; ++c) A[row][c] -= f * A[col][c];
+        }
+    }
+    for (int row = 2; row >= 0; --row) {
+        double acc = A[row][3];
+        for (int c = row + 1; c < 3; ++c) acc -= A[row][c] * s[c];
+        s[row] = acc / A[row][row];
+    }
+    return 0;
+}
+
+static double norminf3(const double *v) {
+    double m = fabs(v[0]);
+    if (fabs(v[1]) > m) m = fabs(v[1]);
+    if (fabs(v[2]) > m) m = fabs(v[2]);
+    return m;
+}
+
+/* Cardano root of h y^3 + (1 - h) y - x = 0 (v = y - y^3 in step 1), then one
+ * Newton correction.  Depressed cubic y^3 + p y + q = 0 with p = (1-h)/h > 0,
+ * q = -x/h; one real root since the discriminant (q/2)^2 + (p/3)^3 > 0.  With
+ * y = u + w, u w = -p/3, u^3 + w^3 = -q, the root is written as
+ * -q / (u^2 - u w + w^2) = -q / (u^2 + p/3 + w^2): a sum of positive terms, so it
+ * loses no digits when q is small. */
+double orc_cardano_cubic(double x, double h)
+{
+    if (x == 0.0) return 0.0;
+    double p = (1.0 - h) / h;
+    double q = -x / h;
+    double disc = (q / 2.0) * (q / 2.0) + (p / 3.0) * (p / 3.0) * (p / 3.0);
+    double sq = sqrt(disc);
+    double u = cbrt(fabs(q) / 2.0 + sq);
+    if (q > 0.0) u = -u;
+    double w = -p / (3.0 * u);
+    double y = -q / (u * u + p / 3.0 + w * w);
+    double f = h * y * y * y + (1.0 - h) * y - x;
+    double fp = 3.0 * h * y * y + (1.0 - h);
+    return y - f / fp;
+}
+
+/* The implicit map F_h of Lemma 4.1: the root c of c = xi + h v(c, mu^X) for an
+ * arbitrary point xi, with mu^X the empirical measure of the array x.  Returns
+ * Newton iterations (0 for closed forms), or -1 when Newton did not converge in
+ * 50 iterations. */
+int orc_implicit_point(const orc_problem *P, const double *x, const double *xi, double *y_out)
+{
+    const int d = P->d;
+    if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
+        y_out[0] = orc_cardano_cubic(xi[0], P->h);
+        return 0;
+    }
+    if (P->coef == ORC_COEF_OU) {
+        for (int c = 0; c < d; ++c) y_out[c] = xi[c] / (1.0 - P->h * P->p[0]);
+        return 0;
+    }
+    /* COUPLED3D: damped Newton from y = x_i. */
+    double y[3] = { xi[0], xi[1], xi[2] };
+    double F[3], J[9], s[3];
+    coupled_residual(P, x, xi, y, F, J);
+    for (int it = 1; it <= 50; ++it) {
+        if (solve3(J, F, s) != 0) return -1;
+        double fn = norminf3(F);
+        double lam = 1.0, yt[3], Ft[3], Jt[9];
+        for (int half = 0; half < 40; ++half) {
+            for (int a = 0; a < 3; ++a) yt[a] = y[a] - lam * s[a];
+            coupled_residual(P, x, xi, yt, Ft, Jt);
+            if (norminf3(Ft) <= fn || half == 39) break;
+            lam *= 0.5;
+        }
+        double step = lam * norminf3(s);
+        for (int a = 0; a < 3; ++a) { y[a] = yt[a]; F[a] = Ft[a]; }
+        memcpy(J, Jt, sizeof J);
+        double scale = norminf3(y) > 1.0 ? norminf3(y) : 1.0;
+        if (step <= 1e-14 * scale) {
+            for (int a = 0; a < 3; ++a) y_out[a] = y[a];
+            return it;
+        }
+    }
+    for (int a = 0; a < 3; ++a) y_out[a] = y[a];
+    return -1;
+}
+
+/* Implicit step for particle i (step 1): y_out[d] = F_h(X_i; mu^X). */
+int orc_implicit_one(const orc_problem *P, const double *x, int64_t i, double *y_out)
+{
+    return orc_implicit_point(P, x, x + (int64_t)P->d * i, y_out);
+}
+
+/* Explicit step for particle i (step 2): x_out[d] = X_{n+1}^i given all Y. */
+void orc_explicit_one(const orc_problem *P, const double *y, int64_t i, int64_t n, double *x_out)
+{
+    const int d = P->d;
+    const double *yi = y + (int64_t)d * i;
+    double b[3], dw[3], sdw[3];
+    drift_b(P, y, yi, b);
+    orc_brownian(P, i, n, dw);
+    diffusion_times_dw(P, yi, dw, sdw);
+    for (int c = 0; c < d; ++c) x_out[c] = yi[c] + P->h * b[c] + sdw[c];
+}
+
+/* Drift b(y_i, mu^Y) for particle i (exposed for component tests). */
+void orc_drift_one(const orc_problem *P, const double *y, int64_t i, double *b_out)
+{
+    drift_b(P, y, y + (int64_t)P->d * i, b_out);
+}
+
+/* Pair sum S and its Jacobian JS for COUPLED3D at an arbitrary point y. */
+void orc_pair_sum_coupled(const orc_problem *P, const double *x, const double *y,
+                          double *S, double *JS)
+{
+    pair_sum_coupled(P, x, y, S, JS);
+}
+
+int orc_implicit_step(const orc_problem *P, const double *x, double *y, int *iters)
+{
+    const int64_t N = P->N;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+    for (int64_t i = 0; i < N; ++i) {
+        int it = orc_implicit_one(P, x, i, y + (int64_t)P->d * i);
+        if (iters) iters[i] = it;
+        if (it < 0) bad += 1;
+    }
+    return bad;
+}
+
+void orc_explicit_step(const orc_problem *P, const double *y, int64_t n, double *xnext)
+{
+    const int64_t N = P->N;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i)
+        orc_explicit_one(P, y, i, n, xnext + (int64_t)P->d * i);
+}
+
+/* X_0^i = x0_mean + x0_std * Z^i, Z from stream 0 at step index 0. */
+void orc_init_x0(const orc_problem *P, double *x)
+{
+    const int d = P->d;
+    for (int64_t i = 0; i < P->N; ++i) {
+        double z[3];
+        orc_normals(P->seed, d, i, 0, 0, z);
+        for (int c = 0; c < d; ++c) x[(int64_t)d * i + c] = P->x0_mean + P->x0_std * z[c];
+    }
+}
+
+/* Raw empirical moments m[k][c] = (1/N) sum_i x_{i,c}^(k+1), k = 0..3. */
+void orc_moments(const orc_problem *P, const double *x, double *m)
+{
+    const int d = P->d;
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < d; ++c) {
+            double s = 0.0;
+            for (int64_t i = 0; i < P->N; ++i) {
+                double v = x[(int64_t)d * i + c], p = v;
+                for (int e = 0; e < k; ++e) p *= v;
+                s += p;
+            }
+            m[k * d + c] = s / (double)P->N;
+        }
+}
+
+/* Advance x (particle-major, N*d) from step n0 through nsteps SSM steps.  If
+ * mom != NULL it receives the moments of X_{n0+s+1} for s = 0..nsteps-1
+ * ([nsteps][4][d]).  Returns the number of failed implicit solves. */
+int orc_run(const orc_problem *P, double *x, int64_t n0, int64_t nsteps, double *mom,
+            int64_t *newton_iters_total)
+{
+    const int64_t nd = P->N * (int64_t)P->d;
+    double *y = (double *)malloc(sizeof(double) * (size_t)nd);
+    int *it = (int *)malloc(sizeof(int) * (size_t)P->N);
+    int bad = 0;
+    int64_t total = 0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        bad += orc_implicit_step(P, x, y, it);
+        for (int64_t i = 0; i < P->N; ++i) total += it[i] > 0 ? it[i] : 0;
+        orc_explicit_step(P, y, n0 + s, x);
+        if (mom) orc_moments(P, x, mom + s * 4 * P->d);
+    }
+    if (newton_iters_total) *newton_iters_total = total;
+    free(y);
+    free(it);
+    return bad;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,310 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, invariants, proven inequalities, high
+precision brute force on tiny systems and the convergence order the paper
+proves.  They run on the CPU (no GPU marker).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 and the normal transform
+# ---------------------------------------------------------------------------
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 matches the published known-answer vectors (SC'11 / Random123)."""
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = O.philox([ctr], key)[0]
+        assert [int(g) for g in got] == want
+
+
+def test_normals_statistics():
+    """X_0 ~ N(0, I) from Philox + Box-Muller: moments and Kolmogorov-Smirnov."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    P = O.problem(d=3, coef=O.COEF_OU, N=1 << 17, h=0.01, seed=12345)
+    z = O.init_x0(P).ravel()
+    n = z.size
+    assert abs(z.mean()) < 5.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    assert abs(np.mean(z ** 3)) < 5.0 * math.sqrt(15.0 / n)
+    assert abs(np.mean(z ** 4) - 3.0) < 5.0 * math.sqrt(96.0 / n)
+    ks = scipy_stats.kstest(z, "norm")
+    assert ks.pvalue > 1e-3
+    # distinct streams and steps give independent draws
+    a = np.array([O.normals(7, 1, i, 0, 1)[0] for i in range(2000)])
+    b = np.array([O.normals(7, 1, i, 1, 1)[0] for i in range(2000)])
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.1
+
+
+def test_brownian_fine_sum_is_consistent():
+    """A coarse increment equals the sum of the fine increments it covers (same path)."""
+    Pf = O.problem(d=3, coef=O.COEF_COUPLED3D, N=4, h=2.0 ** -6, seed=3, fine_log2=6)
+    Pc = O.problem(d=3, coef=O.COEF_COUPLED3D, N=4, h=2.0 ** -4, seed=3, fine_log2=6)
+    for i in range(4):
+        coarse = O.brownian(Pc, i, 1)
+        fine = sum(O.brownian(Pf, i, 4 + k) for k in range(4))
+        assert np.allclose(coarse, fine, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Implicit step: closed forms and Lemma 4.1
+# ---------------------------------------------------------------------------
+
+def test_cardano_matches_high_precision_root():
+    """Root of h y^3 + (1-h) y - x = 0 (v = y - y^3) to within 2 ulp of a 50-digit root."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for h in (1e-2, 2.0 ** -4, 2.0 ** -10, 0.3):
+        for x in list(inputs.uniform_points(40, -6.0, 6.0, seed=11)) + [0.0, 1e-300, -2.5e-9]:
+            y = O.cardano(x, h)
+            f = lambda t: mp.mpf(h) * t ** 3 + (1 - mp.mpf(h)) * t - mp.mpf(x)
+            lo, hi = mp.mpf(-10), mp.mpf(10)
+            for _ in range(1100):   # bisection on the increasing cubic, down to 1e-320
+                mid = (lo + hi) / 2
+                if f(mid) > 0:
+                    hi = mid
+                else:
+                    lo = mid
+            exact = float((lo + hi) / 2)
+            assert abs(y - exact) <= 2 * np.spacing(abs(exact)) + 1e-320, (x, h, y, exact)
+
+
+def test_linear_implicit_remark():
+    """Remark 4.3: v = 10 x gives y = x / (1 - 10 h) (exact up to one rounding)."""
+    P = O.problem(d=1, coef=O.COEF_OU, N=5, h=0.05, p=(10.0, 0.0, 0.0))
+    x = inputs.gaussian_cloud(5, 1, seed=2)
+    y, it, bad = O.implicit_step(P, x)
+    assert bad == 0
+    assert np.allclose(y, x * 2.0, rtol=2e-16, atol=0)   # 1 / (1 - 0.5) = 2
+
+
+@pytest.mark.parametrize("coef,d,Lv", [(O.COEF_CUBIC1D_GAUSS, 1, 1.0),
+                                       (O.COEF_COUPLED3D, 3, 1.0 / 16.0)])
+def test_lemma_4_1_inequalities(coef, d, Lv):
+    """Lemma 4.1 (4.1), (4.2), (4.5) for the implicit map F_h with a frozen measure.
+
+    L_v: v = x - x^3 has one-sided constant 1.  For the coupled set, -y|y|^2 is
+    monotone and the pair term's Jacobian has eigenvalues at most
+    max_r 0.5 (r^2 - 1) / (1 + r^2)^2 = 1/16.
+    """
+    h = 2.0 ** -4
+    P = O.problem(d=d, coef=coef, N=48, h=h)
+    mu = inputs.gaussian_cloud(48, d, seed=5)
+    pts = inputs.gaussian_cloud(60, d, seed=6, scale=1.5)
+
+    def v(point):
+        point = np.asarray(point, float)
+        if coef == O.COEF_CUBIC1D_GAUSS:
+            return point - point ** 3
+        dd = mu - point
+        w = 1.0 / (1.0 + np.sum(dd * dd, axis=1))
+        return -point * np.dot(point, point) + 0.5 * np.mean(dd * w[:, None], axis=0)
+
+    F = [O.implicit_point(P, mu, p)[0] for p in pts]
+    for a in range(0, 60, 2):
+        x, y = pts[a], pts[a + 1]
+        Fx, Fy = F[a], F[a + 1]
+        vhx, vhy = (Fx - x) / h, (Fy - y) / h           # v_h = v(F_h) = (F_h - x)/h
+        assert np.allclose(vhx, v(Fx), rtol=1e-9, atol=1e-9)
+        # (4.1) |v_h(x)| <= |v(x)| / (1 - h L_v)
+        assert np.linalg.norm(vhx) <= np.linalg.norm(v(x)) / (1 - h * Lv) * (1 + 1e-12) + 1e-12
+        # (4.2) |F_h(x) - F_h(y)|^2 <= |x - y|^2 / (1 - 2 h L_v)
+        assert np.sum((Fx - Fy) ** 2) <= np.sum((x - y) ** 2) / (1 - 2 * h * Lv) * (1 + 1e-12)
+        # (4.5) <x - y, v_h(x) - v_h(y)> <= L_v / (1 - 2 h L_v) |x - y|^2
+        assert np.dot(x - y, vhx - vhy) <= Lv / (1 - 2 * h * Lv) * np.sum((x - y) ** 2) + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Pairwise interaction: invariants
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("coef,d", [(O.COEF_CUBIC1D_GAUSS, 1), (O.COEF_COUPLED3D, 3)])
+def test_drift_is_antisymmetric_and_translation_invariant(coef, d):
+    """sum_i b(Y_i, mu^Y) = 0 (antisymmetric pair kernel, self term zero) and
+    b(Y + c, mu^{Y + c}) = b(Y, mu^Y)."""
+    N = 300
+    P = O.problem(d=d, coef=coef, N=N, h=0.01)
+    y = inputs.gaussian_cloud(N, d, seed=8)
+    b = np.array([O.drift_one(P, y, i) for i in range(N)])
+    assert np.all(np.abs(b.sum(axis=0)) <= N * 4e-16 * np.abs(b).max() * 4)
+    shift = np.array([0.75, -0.5, 0.25][:d])
+    b2 = np.array([O.drift_one(P, y + shift, i) for i in range(N)])
+    assert np.allclose(b, b2, rtol=0, atol=1e-14)
+
+
+def test_coupled_pair_sum_at_x_sums_to_zero_and_jacobian_is_derivative():
+    """At Y = X the pair part of v sums to zero over particles; JS is dS/dy
+    (checked by central differences)."""
+    N = 200
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=0.01)
+    x = inputs.gaussian_cloud(N, 3, seed=9)
+    tot = np.zeros(3)
+    for i in range(N):
+        S, _ = O.pair_sum_coupled(P, x, x[i])
+        tot += S
+    assert np.all(np.abs(tot) < 1e-13)
+    y0 = np.array([0.3, -0.7, 1.1])
+    _, JS = O.pair_sum_coupled(P, x, y0)
+    eps = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = eps
+        Sp, _ = O.pair_sum_coupled(P, x, y0 + e)
+        Sm, _ = O.pair_sum_coupled(P, x, y0 - e)
+        assert np.allclose((Sp - Sm) / (2 * eps), JS[:, c], rtol=0, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Whole step: brute force at N <= 8 in 40-digit arithmetic
+# ---------------------------------------------------------------------------
+
+def _brute_step(mp, coef, x, dw, h):
+    """One SSM step in high precision: step 1 by fixed-point iteration
+    Y <- X + h v(Y, mu^X) (a contraction for these h and |x|), step 2 as written."""
+    N, d = len(x), len(x[0])
+    X = [[mp.mpf(float(v)) for v in row] for row in x]
+    H = mp.mpf(h)
+
+    def v(yi):
+        if coef == O.COEF_CUBIC1D_GAUSS:
+            return [yi[0] - yi[0] ** 3]
+        s = [mp.mpf(0)] * 3
+        for xj in X:
+            dd = [xj[c] - yi[c] for c in range(3)]
+            w = 1 / (1 + sum(t * t for t in dd))
+            s = [s[c] + dd[c] * w for c in range(3)]
+        r2 = sum(t * t for t in yi)
+        return [-yi[c] * r2 + s[c] / (2 * N) for c in range(3)]
+
+    Y = []
+    for xi in X:
+        yi = list(xi)
+        for _ in range(400):
+            vi = v(yi)
+            yn = [xi[c] + H * vi[c] for c in range(d)]
+            if max(abs(yn[c] - yi[c]) for c in range(d)) < mp.mpf(10) ** -38:
+                yi = yn
+                break
+            yi = yn
+        Y.append(yi)
+    out = []
+    for i, yi in enumerate(Y):
+        s = [mp.mpf(0)] * d
+        for yj in Y:
+            dd = [yj[c] - yi[c] for c in range(d)]
+            r2 = sum(t * t for t in dd)
+            e = mp.exp(-r2) if coef == O.COEF_CUBIC1D_GAUSS else mp.exp(-r2 / 2)
+            s = [s[c] + dd[c] * e for c in range(d)]
+        if coef == O.COEF_CUBIC1D_GAUSS:
+            b = [mp.mpf("0.5") * s[0] / N]
+            sig = [mp.mpf("0.4") * yi[0] + mp.mpf("0.1")]
+        else:
+            b = [s[c] / N for c in range(3)]
+            sig = [mp.mpf("0.3") * yi[c] + mp.mpf("0.2") for c in range(3)]
+        out.append([yi[c] + H * b[c] + sig[c] * mp.mpf(float(dw[i][c])) for c in range(d)])
+    return np.array([[float(t) for t in r] for r in Y]), np.array([[float(t) for t in r] for r in out])
+
+
+@pytest.mark.parametrize("coef,d,N", [(O.COEF_CUBIC1D_GAUSS, 1, 7), (O.COEF_COUPLED3D, 3, 5),
+                                      (O.COEF_COUPLED3D, 3, 1), (O.COEF_CUBIC1D_GAUSS, 1, 2)])
+def test_whole_step_matches_high_precision_brute_force(coef, d, N):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    h = 2.0 ** -6
+    P = O.problem(d=d, coef=coef, N=N, h=h, seed=21)
+    x = inputs.gaussian_cloud(N, d, seed=30 + N, scale=1.2)
+    n = 3
+    dw = np.array([O.brownian(P, i, n) for i in range(N)])
+    y, it, bad = O.implicit_step(P, x)
+    assert bad == 0
+    xn = O.explicit_step(P, y, n)
+    yb, xb = _brute_step(mp, coef, x, dw, h)
+    assert np.allclose(y, yb, rtol=0, atol=2e-15)
+    assert np.allclose(xn, xb, rtol=0, atol=4e-15)
+
+
+# ---------------------------------------------------------------------------
+# Whole run: the linear (OU) case, §3.4.1
+# ---------------------------------------------------------------------------
+
+def test_ou_sample_mean_follows_exact_linear_recursion():
+    """For v = rho x, b = lambda E[X], sigma = eta the scheme is linear, so the
+    particle mean obeys mean' = mean (1 + h lambda) / (1 - h rho) + eta mean(dW)
+    exactly (step 1 divides by 1 - h rho, step 2 adds h lambda mean(Y)).  A
+    measure taken at X instead of Y in step 2, a dropped self term or a 1/(N-1)
+    weight all break it."""
+    rho, lam, eta = -1.0, 0.5, 0.5
+    N, h, M = 64, 2.0 ** -5, 32
+    P = O.problem(d=1, coef=O.COEF_OU, N=N, h=h, seed=4, p=(rho, lam, eta), x0_mean=1.0, x0_std=0.5)
+    x = O.init_x0(P)
+    mean = x.mean()
+    xs = x
+    for n in range(M):
+        xs = O.run(P, xs, n, 1)
+        dwbar = np.mean([O.brownian(P, i, n)[0] for i in range(N)])
+        mean = mean * (1 + h * lam) / (1 - h * rho) + eta * dwbar
+        assert abs(xs.mean() - mean) < 1e-13
+
+
+def test_ou_moments_match_paper_closed_form():
+    """E[X_t] = x0 e^{(rho+lambda)t}, E[X_t^2] = x0^2 e^{2(rho+lambda)t}
+    + eta^2/(2 rho)(e^{2 rho t} - 1) (§3.4.1), within O(h) bias plus 5 standard
+    errors of the particle average."""
+    rho, lam, eta, x0 = -1.0, 0.5, 0.5, 1.0
+    N, h, T = 1 << 14, 2.0 ** -7, 1.0
+    M = int(round(T / h))
+    P = O.problem(d=1, coef=O.COEF_OU, N=N, h=h, seed=17, p=(rho, lam, eta), x0_mean=x0, x0_std=0.0)
+    x = O.run(P, O.init_x0(P), 0, M)
+    m1 = np.exp((rho + lam) * T) * x0
+    m2 = x0 ** 2 * np.exp(2 * (rho + lam) * T) + eta ** 2 / (2 * rho) * (np.exp(2 * rho * T) - 1)
+    var = m2 - m1 ** 2
+    se1 = math.sqrt(var / N)
+    se2 = math.sqrt((3 * var ** 2 + 4 * m1 ** 2 * var) / N)
+    bias = 2.0 * h   # first-order-in-h discretisation bias of the linear scheme
+    assert abs(x.mean() - m1) < bias + 5 * se1
+    assert abs(np.mean(x ** 2) - m2) < bias + 5 * se2
+
+
+# ---------------------------------------------------------------------------
+# Convergence order, Theorem 2.3: rMSE <= C h^{1/2}
+# ---------------------------------------------------------------------------
+
+def test_strong_error_decays_at_least_at_rate_one_half():
+    """rMSE at T against an h = 2^-12 run on the same Brownian paths (§3's proxy
+    for the true solution) decreases with h at a fitted log-log slope >= 0.45."""
+    N, L, T = 96, 12, 1.0
+    ref_P = O.problem(d=1, coef=O.COEF_CUBIC1D_GAUSS, N=N, h=2.0 ** -L, seed=31, fine_log2=L)
+    x0 = O.init_x0(ref_P)
+    ref = O.run(ref_P, x0, 0, 1 << L)
+    hs, errs = [], []
+    for k in range(3, 8):
+        P = O.problem(d=1, coef=O.COEF_CUBIC1D_GAUSS, N=N, h=2.0 ** -k, seed=31, fine_log2=L)
+        xk = O.run(P, x0, 0, 1 << k)
+        hs.append(2.0 ** -k)
+        errs.append(math.sqrt(np.mean((xk - ref) ** 2)))
+    slope = np.polyfit(np.log2(hs), np.log2(errs), 1)[0]
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1)), errs
+    assert slope >= 0.45, (slope, errs)
