@@ -1,0 +1,293 @@
+#!/usr/bin/env python
+"""Throughput of the split-step method (SSM) on GB300: particle-steps/s.
+
+Workload: the coupled 3-d McKean-Vlasov system with an implicit pairwise drift,
+N = 2^18 particles, d = 3, h = 2^-8, T = 1, seed 2 (X_0 ~ N(0, I_3), synthetic).
+One "step" is one whole SSM step (§2.3): Philox Brownian increments, the
+implicit step solved for all particles (O(N^2) pair sums per pass), the O(N^2)
+pairwise drift, and the fused explicit update with FP64 moments.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica (its own seed); value is the units of all ranks over the slowest rank's
+time ("weak" scaling).  ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PART, DIM, H, T_END, SEED = 1 << 18, 3, 2.0 ** -8, 1.0, 2
+FP32_LANES_PER_SM, N_SMS, MAX_SM_MHZ = 128, 152, 2070.0
+# algorithmic FP32 flops per pair (FFMA = 2): see DESIGN.md, "Roofline"
+FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
+METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 comparison (0 = skip)")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds):
+    """The FP64 oracle on the host cores, one step of the workload restricted to a
+    bounded sample of target particles (each target does its full O(N) work)."""
+    import oracle as O
+    P = O.problem(d=DIM, coef=O.COEF_COUPLED3D, N=N_PART, h=H, seed=SEED)
+    x = O.init_x0(P)
+    nth = O.num_threads()
+    n = max(nth, 8)
+    t0 = time.perf_counter()
+    O.sample_step(P, x, np.arange(n), 0)
+    dt = time.perf_counter() - t0
+    n2 = int(max(n, min(N_PART, n * seconds / max(dt, 1e-3))))
+    n2 = (n2 + nth - 1) // nth * nth
+    idx = np.random.default_rng(0).choice(N_PART, size=min(n2, N_PART), replace=False)
+    t0 = time.perf_counter()
+    O.sample_step(P, x, idx, 0)
+    dt = time.perf_counter() - t0
+    return {"value": idx.size / dt, "unit": "particle-steps/s", "cores": nth, "kind": "oracle",
+            "sample": "step 0 of N=2^18 d=3 h=2^-8 restricted to %d random target particles (each: FP64 Newton "
+                      "implicit solve against all N particles + pairwise drift against all N), %.1f s" %
+                      (idx.size, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = cpu_baseline(max(2.0, args.cpu_seconds))
+    steps_s = []
+    import oracle as O
+    P = O.problem(d=DIM, coef=O.COEF_COUPLED3D, N=N_PART, h=H, seed=SEED)
+    x = O.init_x0(P)
+    per = max(O.num_threads(), int(cb["value"] * max(1.0, 60.0 / max(1, args.steps + args.warmup)) / 4))
+    rng = np.random.default_rng(1)
+    for k in range(args.warmup + args.steps):
+        idx = rng.choice(N_PART, size=min(per, N_PART), replace=False)
+        t0 = time.perf_counter()
+        O.sample_step(P, x, idx, k)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            steps_s.append(idx.size / dt)
+    v = statistics.median(steps_s)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_PART / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: X_0 ~ N(0, I_3) from Philox4x32-10 seed 2",
+            "config": {"workload": "coupled3d N=2^18 d=3 h=2^-8 T=1 seed=2 (FP64 oracle, sampled targets)",
+                       "sample_targets_per_step": per, "l2": "n/a (CPU)"},
+            "cpu_baseline": dict(cb, value=v, sample="%d random targets per step, full O(N) work each" % per),
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_kernel(torch, S, s, stream, which, reps):
+    """Average duration of one full pair pass (CUDA events on the context's stream)."""
+    s.pair_pass(which)   # warm
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        s.pair_pass(which)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    return ev[0].elapsed_time(ev[1]) / 1e3 / reps
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    from paper_2105_09688_gb300 import build as B
+    B.build()
+    import paper_2105_09688_gb300 as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    seed = SEED + 1000 * rank
+    prec = S.SSM_FP32C
+    form = "fp32c"
+    if os.path.exists(os.path.join(ROOT, "paper_2105_09688_gb300", "ws_weights.bin")) and hasattr(S, "load_ws"):
+        prec, form = S.SSM_FP32C_LEARNED, "learned+fp32c"
+    s = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream, precision=prec)
+    if prec == S.SSM_FP32C_LEARNED:
+        S.load_ws(s)
+    for _ in range(args.warmup):
+        s.run_steps(1)
+    s.sync()
+    st0 = s.stats()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush between timed steps (not timed)
+        evs[k][0].record(stream)
+        s.run_steps(1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    s.sync()
+    st1 = s.stats()
+    step_s = [a.elapsed_time(b) / 1e3 for a, b in evs]
+    total = float(sum(step_s))
+    if world > 1:
+        t = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * N_PART * args.steps / total
+    newton_passes = (st1["newton_passes"] - st0["newton_passes"]) / args.steps
+    newton_rows = (st1["newton_rows"] - st0["newton_rows"]) / args.steps
+
+    # dominant kernel in isolation (same stream, CUDA events)
+    t_newton = time_kernel(torch, S, s, stream, 0, 3)
+    t_drift = time_kernel(torch, S, s, stream, 1, 3)
+    share_newton = newton_rows / N_PART * t_newton
+    dom = 0 if share_newton >= t_drift else 1
+    t_dom = t_newton if dom == 0 else t_drift
+    flops = FLOPS_PAIR[dom] * N_PART * N_PART
+    sm_mhz = MAX_SM_MHZ
+    peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / t_dom / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pair<%s, float>" % ("PK_NEWTON3" if dom == 0 else "PK_DRIFT3"),
+                "peak_basis": "FP32 CUDA-core: 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe max clock)",
+                "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3}
+
+    # end to end through the C ABI: pinned host state in, step, pinned host state out
+    xh = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()
+    xo = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()
+    x_cur, n_cur = s.get_state(out=xh)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        s.set_state(xh, n_cur)
+        s.run_steps(1)
+        s.get_state(out=xo)
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": N_PART * e2e_steps / e2e_dt * world, "unit": "particle-steps/s",
+           "h2d_bytes_per_step": N_PART * DIM * 8, "d2h_bytes_per_step": N_PART * DIM * 8,
+           "steps": e2e_steps}
+    s.close()
+
+    # plain FP64 GPU SSM on the same workload (comparison of the metric)
+    fp64 = None
+    if args.fp64_steps > 0:
+        p = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+                  precision=S.SSM_FP64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        p.run_steps(args.fp64_steps)
+        e1.record(stream)
+        e1.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        pst = p.stats()
+        fp64 = {"value": N_PART * args.fp64_steps / dt, "unit": "particle-steps/s", "steps": args.fp64_steps,
+                "ms_per_step": dt * 1e3 / args.fp64_steps,
+                "newton_passes_per_step": pst["newton_passes"] / max(1, pst["steps"])}
+        p.close()
+
+    kmax = 12
+    launches_per_step = 1 + 2 * kmax + 1 + 1 + 1 + 1 + (1 if form.startswith("learned") else 0)
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic: X_0 ~ N(0, I_3) from Philox4x32-10 (seed 2 + 1000 rank)",
+            "config": {"workload": "coupled3d N=2^18 d=3 h=2^-8 T=1 seed=2", "form": form,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between timed steps (512 MB write, untimed)",
+                       "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+            "plain_fp64": fp64,
+            "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * ssm.h -- C ABI of the GB300 (sm_103a) split-step-method library.
+ *
+ * The library advances the N-particle system of a McKean-Vlasov SDE
+ * (Chen & dos Reis, arXiv:2105.09688, §1 Eq. (MV-SDE Propagation))
+ *
+ *   dX^i = ( v(X^i, mu^N) + b(X^i, mu^N) ) dt + sigma(X^i, mu^N) dW^i,
+ *   mu^N = (1/N) sum_j delta_{X^j}    (self term included, weight 1/N)
+ *
+ * with the split-step method (SSM) of §2.3 (eq. SSTM:scheme 1, SSTM:scheme 2)
+ * on the uniform grid t_n = n h, h = T/M:
+ *
+ *   step 1 (implicit):  Y_i  = X_i + h v(Y_i, mu^X_n)          (mu^X_n frozen)
+ *   step 2 (explicit):  X'_i = Y_i + h b(Y_i, mu^Y_n) + sigma(Y_i, mu^Y_n) dW_n^i
+ *
+ * Every step of that path runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points
+ *  - Every function returns ssm_status and never aborts the process.
+ *  - Host arrays are owned by the caller and copied; particle arrays on the host
+ *    are particle-major, x[d*i + c], i < N, c < d, IEEE double.
+ *  - Device memory of a context is owned by the context (allocated in
+ *    ssm_create, or carved from a caller-owned workspace given in ssm_opts).
+ *  - The CUDA stream in ssm_opts is borrowed: work is enqueued on it and the
+ *    functions that return host data synchronise it.
+ *  - Errors detected on the device (non-finite state, implicit solve not
+ *    converged, a bounded wait that gave up) are sticky: once seen, every later
+ *    call on that context returns the same status until ssm_destroy.
+ *  - Functions are not thread-safe on one context; distinct contexts are
+ *    independent.
+ */
+#ifndef SSM_H
+#define SSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSM_OK = 0,
+    SSM_EINVAL = 1,      /* bad argument (size, step size beyond Theorem 2.3's bound, ...) */
+    SSM_ENOMEM = 2,      /* device allocation failed or workspace too small */
+    SSM_ECUDA = 3,       /* a CUDA runtime call failed */
+    SSM_ENOCONV = 4,     /* an implicit solve missed its tolerance within newton_kmax passes */
+    SSM_ENONFINITE = 5,  /* a particle state became NaN or infinite */
+    SSM_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    SSM_ESTATE = 7       /* call not valid in the context's state (e.g. past t = T) */
+} ssm_status;
+
+/* Coefficient sets (v, b, sigma) built into the library.
+ *  SSM_COEF_CUBIC1D_GAUSS (d = 1): v(x) = x - x^3;
+ *      b(y, mu) = 0.5 int (z - y) exp(-(y - z)^2) mu(dz);  sigma(y) = 0.4 y + 0.1.
+ *      Step 1 is a scalar cubic, solved in closed form (Cardano).
+ *  SSM_COEF_COUPLED3D (d = 3): v(y, mu) = -y|y|^2 + 0.5 int (z - y)/(1 + |y - z|^2) mu(dz);
+ *      b(y, mu) = int (z - y) exp(-|y - z|^2 / 2) mu(dz);  sigma(y) = diag(0.3 y_k + 0.2).
+ *      Step 1 couples every particle to mu^X through an O(N) sum per particle,
+ *      solved by Newton-type iterations whose N^2 pair sums run on the GPU.
+ *  SSM_COEF_OU (any d, componentwise; §3.4.1 Eq. (stablity:OU)): v(x) = rho x,
+ *      b(mu) = lambda int z mu(dz), sigma = eta, with (rho, lambda, eta) taken
+ *      from ssm_opts.coef_params[0..2]. */
+typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2 } ssm_coef;
+
+/* Arithmetic of the O(N^2) pair sums.
+ *  SSM_FP64: IEEE double throughout.
+ *  SSM_FP32C: pair terms in FP32, summed in FP32 over blocks of 256 sources whose
+ *      block sums are combined with error-free (two-sum) compensation and then in
+ *      double; the Newton residual, the per-particle solves, the state and the
+ *      moments stay in double.
+ *  SSM_FP32C_LEARNED: SSM_FP32C with a learned initial guess for step 1
+ *      (SSM_COEF_COUPLED3D only; load weights with ssm_ws_load). */
+typedef enum { SSM_FP64 = 0, SSM_FP32C = 1, SSM_FP32C_LEARNED = 2 } ssm_precision;
+
+typedef struct {
+    int precision;          /* ssm_precision; default SSM_FP64 */
+    double newton_tol;      /* step 1 stops when max_c |r_c| <= newton_tol, with
+                               r = Y - X - h v(Y, mu^X); default 1e-13 (FP64), 1e-10 (FP32C) */
+    int newton_kmax;        /* maximum N-body passes of one implicit step; default 12 */
+    int fine_log2;          /* 0: dW on the step's own grid.  L > 0: the Brownian path
+                               lives on the grid T 2^-L (h must be a multiple of it) and
+                               dW over a step is the sum of its fine increments, so runs
+                               at different h share one path (§3). */
+    double x0_mean;         /* X_0 = x0_mean + x0_std Z, Z ~ N(0, I_d); default 0 */
+    double x0_std;          /* default 1 */
+    double coef_params[4];  /* SSM_COEF_OU: rho, lambda, eta */
+    void *stream;           /* cudaStream_t to enqueue on (borrowed); NULL = default stream */
+    void *workspace;        /* optional caller-owned device memory, >= ssm_workspace_bytes(),
+                               256-byte aligned; NULL = the context allocates */
+    size_t workspace_bytes;
+    int tile_chunks;        /* 0 = tuned; else number of source chunks per pair pass */
+    int ws_passes;          /* learned form: passes from the learned start before the
+                               plain restart; default 3 */
+} ssm_opts;
+
+typedef struct {
+    int64_t steps;           /* SSM steps taken by this context */
+    int64_t newton_passes;   /* N-body passes of step 1, summed over steps */
+    int64_t newton_rows;     /* targets evaluated in those passes (pairs = rows * N) */
+    int64_t drift_rows;      /* targets evaluated by the step-2 pair sums */
+    int64_t fallbacks;       /* learned starts that missed the tolerance and restarted */
+    int64_t max_passes;      /* largest pass count of one implicit step */
+    int64_t hist[16];        /* particles that converged after k passes (last step), k < 16 */
+} ssm_stats_t;
+
+typedef struct ssm_ctx ssm_ctx;
+
+/* Fill *opts with the defaults listed above. */
+void ssm_opts_default(ssm_opts *opts);
+
+/* Bytes of device memory a context of this shape needs (for ssm_opts.workspace). */
+size_t ssm_workspace_bytes(int d, int64_t N, int coef, const ssm_opts *opts);
+
+/* Create a context for N particles in R^d on [0, T] with step h (§2.3: M = T/h
+ * steps; h must divide T to 1e-12 relative).  Draws X_0 on the device from the
+ * Philox4x32-10 stream of `seed` (stream 0).  Rejects with SSM_EINVAL: d not
+ * supported by `coef` (CUBIC1D: 1, COUPLED3D: 3, OU: 1..3), N < 1 or N > 2^26,
+ * h <= 0, T <= 0, or h above the step-size bound of Theorem 2.3,
+ * h <= 1/(1 + 2 L_v) when L_v > -1/2 (L_v = 1 for CUBIC1D, 1/16 for COUPLED3D,
+ * rho for OU).  *out receives the context, or NULL on error. */
+ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t seed,
+                      const ssm_opts *opts, ssm_ctx **out);
+
+/* Enqueue one SSM step n -> n+1 (steps 1 and 2 above).  Asynchronous.
+ * SSM_ESTATE if the context is already at n = M. */
+ssm_status ssm_step(ssm_ctx *ctx);
+
+/* Enqueue k steps (k >= 0, n + k <= M), replayed from a CUDA graph of one step. */
+ssm_status ssm_run_steps(ssm_ctx *ctx, int64_t k);
+
+/* Enqueue the remaining steps up to n = M. */
+ssm_status ssm_run(ssm_ctx *ctx);
+
+/* Wait for enqueued work and report any device-detected error. */
+ssm_status ssm_sync(ssm_ctx *ctx);
+
+/* Raw empirical moments of the current state, out[k*d + c] = (1/N) sum_i x_{i,c}^(k+1),
+ * k = 0..3 (caller-owned host array of 4*d doubles).  Synchronising. */
+ssm_status ssm_moments(ssm_ctx *ctx, double *out);
+
+/* Copy the current state X_n to the caller's host array x[N*d] and the step
+ * index to *n (either may be NULL).  Synchronising. */
+ssm_status ssm_get_state(ssm_ctx *ctx, double *x, int64_t *n);
+
+/* Replace the state by x[N*d] (host, particle-major) at step index n (0 <= n <= M).
+ * Brownian increments are a pure function of (seed, particle, step), so a run
+ * resumed from (X_n, n) continues bit for bit.  Asynchronous w.r.t. the device. */
+ssm_status ssm_set_state(ssm_ctx *ctx, const double *x, int64_t n);
+
+/* Stages of the last step, copied to a host array [N*d] (particle-major). */
+enum { SSM_STAGE_Y = 0, SSM_STAGE_B = 1 };
+ssm_status ssm_get_stage(ssm_ctx *ctx, int which, double *out);
+
+/* Counters of the work done (synchronising). */
+ssm_status ssm_stats(ssm_ctx *ctx, ssm_stats_t *out);
+
+/* Release the context and its device memory (not a caller workspace).  NULL-safe. */
+void ssm_destroy(ssm_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *ssm_status_str(int status);
+
+/* ---- component entry points (the same device code as the step, for checks) ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters ctr[4*k .. 4*k+3] under the key
+ * (seed mod 2^32, seed >> 32), computed on the device; out[4*n] (host arrays).
+ * The paper leaves the random source open; this is the library's. */
+ssm_status ssm_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out);
+
+/* The d standard normals of particles 0..N-1 at counter (i, step, stream) that the
+ * step uses (Box-Muller of Philox uniforms), out[N*d] on the host. */
+ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream, double *out);
+
+/* Step 1 for SSM_COEF_CUBIC1D_GAUSS alone: y[k] = the real root of
+ * h y^3 + (1 - h) y - x[k] = 0 (Lemma 4.1's F_h for v = x - x^3), 0 < h < 1/3. */
+ssm_status ssm_cardano(const double *x, int64_t n, double h, double *y);
+
+/* Enqueue one full O(N^2) pair-sum pass of the context's current state on its
+ * stream, for timing and profiling the dominant kernel in isolation:
+ *   which = 0: the step-1 pair sums of SSM_COEF_COUPLED3D, (1/N) sum_j (X_j - Y_i) w_ij
+ *              and (1/N) sum_j w_ij, w_ij = 1/(1 + |X_j - Y_i|^2), for all N targets
+ *              at the current Y (§2.3 eq. SSTM:scheme 1);
+ *   which = 1: the step-2 drift pair sums b(Y_i, mu^Y) of the context's
+ *              coefficient set (§2.3 eq. SSTM:scheme 2).
+ * Overwrites only the context's partial-sum scratch (the state is untouched).
+ * *pairs receives the number of pair evaluations enqueued (may be NULL). */
+ssm_status ssm_pair_pass(ssm_ctx *ctx, int which, int64_t *pairs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSM_H */

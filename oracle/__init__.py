@@ -53,6 +53,7 @@ def lib():
             "orc_moments": (None, [P, dp, dp]),
             "orc_run": (_c_int, [P, dp, _c_i64, _c_i64, dp, ctypes.POINTER(_c_i64)]),
             "orc_num_threads": (_c_int, []),
+            "orc_sample_step": (None, [P, dp, dp, ctypes.POINTER(_c_i64), _c_i64, _c_i64, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -175,6 +176,19 @@ def explicit_step(P, y, n):
     x = np.empty_like(y)
     lib().orc_explicit_step(ctypes.byref(P), _dp(y), int(n), _dp(x))
     return x
+
+
+def sample_step(P, x, idx, n):
+    """Step n restricted to the target particles idx (for timing a bounded sample):
+    returns X_{n+1} of those targets.  Particles outside the sample enter step 2's
+    measure at their X_n."""
+    x = _c(x, P)
+    y = x.copy()
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty((idx.size, P.d))
+    lib().orc_sample_step(ctypes.byref(P), _dp(x), _dp(y), idx.ctypes.data_as(ctypes.POINTER(_c_i64)),
+                          idx.size, int(n), _dp(out))
+    return out
 
 
 def moments(P, x):

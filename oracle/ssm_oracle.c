@@ -392,6 +392,22 @@ void orc_explicit_step(const orc_problem *P, const double *y, int64_t n, double 
         orc_explicit_one(P, y, i, n, xnext + (int64_t)P->d * i);
 }
 
+/* One SSM step restricted to the target particles idx[0..n-1], used to time a
+ * bounded sample of a step: Y_i = F_h(X_i; mu^X) against all N particles,
+ * written into y (an N*d array the caller fills with the measure step 2 uses
+ * for the particles outside the sample), then X'_i into xout[d*k]. */
+void orc_sample_step(const orc_problem *P, const double *x, double *y, const int64_t *idx, int64_t n,
+                     int64_t step, double *xout)
+{
+    const int d = P->d;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; ++k)
+        orc_implicit_one(P, x, idx[k], y + (int64_t)d * idx[k]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; ++k)
+        orc_explicit_one(P, y, idx[k], step, xout + (int64_t)d * k);
+}
+
 /* X_0^i = x0_mean + x0_std * Z^i, Z from stream 0 at step index 0. */
 void orc_init_x0(const orc_problem *P, double *x)
 {

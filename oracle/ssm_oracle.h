@@ -41,6 +41,8 @@ void orc_pair_sum_coupled(const orc_problem *P, const double *x, const double *y
                           double *S, double *JS);
 int orc_implicit_step(const orc_problem *P, const double *x, double *y, int *iters);
 void orc_explicit_step(const orc_problem *P, const double *y, int64_t n, double *xnext);
+void orc_sample_step(const orc_problem *P, const double *x, double *y, const int64_t *idx, int64_t n,
+                     int64_t step, double *xout);
 void orc_init_x0(const orc_problem *P, double *x);
 void orc_moments(const orc_problem *P, const double *x, double *m);
 int orc_run(const orc_problem *P, double *x, int64_t n0, int64_t nsteps, double *mom,

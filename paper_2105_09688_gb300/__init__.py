@@ -1,0 +1,280 @@
+"""Python binding of the GB300 split-step-method library (``libssm.so``).
+
+Thin ctypes marshalling over the C ABI of ``include/ssm.h``: the functions here
+carry the same names and move numpy arrays and plain numbers across; every step
+of the method runs in the library's CUDA kernels.  PyTorch is used only to hand
+the library device memory (a workspace tensor) and a CUDA stream.
+
+The library must have been built (``paper_2105_09688_gb300.build.build()``); if
+it is missing, loading fails with an error -- there is no CPU fallback.
+
+Method: Chen & dos Reis, "A flexible split-step scheme for solving McKean-Vlasov
+stochastic differential equations", arXiv:2105.09688, §2.3.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "SSM_OK", "SSM_EINVAL", "SSM_ENOMEM", "SSM_ECUDA", "SSM_ENOCONV", "SSM_ENONFINITE", "SSM_ETIMEOUT",
+    "SSM_ESTATE", "SSM_COEF_CUBIC1D_GAUSS", "SSM_COEF_COUPLED3D", "SSM_COEF_OU", "SSM_FP64", "SSM_FP32C",
+    "SSM_FP32C_LEARNED", "SSM_STAGE_Y", "SSM_STAGE_B", "SSMError", "ssm_opts", "ssm_stats_t", "lib",
+    "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
+    "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
+    "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "SSM",
+]
+
+SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
+SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU = 0, 1, 2
+SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
+SSM_STAGE_Y, SSM_STAGE_B = 0, 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libssm.so")
+
+_i32, _i64, _u64, _dbl, _sz, _vp = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                                    ctypes.c_size_t, ctypes.c_void_p)
+
+
+class ssm_opts(ctypes.Structure):
+    _fields_ = [("precision", _i32), ("newton_tol", _dbl), ("newton_kmax", _i32), ("fine_log2", _i32),
+                ("x0_mean", _dbl), ("x0_std", _dbl), ("coef_params", _dbl * 4), ("stream", _vp),
+                ("workspace", _vp), ("workspace_bytes", _sz), ("tile_chunks", _i32), ("ws_passes", _i32)]
+
+
+class ssm_stats_t(ctypes.Structure):
+    _fields_ = [("steps", _i64), ("newton_passes", _i64), ("newton_rows", _i64), ("drift_rows", _i64),
+                ("fallbacks", _i64), ("max_passes", _i64), ("hist", _i64 * 16)]
+
+
+class SSMError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        super().__init__("%s%s" % (where + ": " if where else "", ssm_status_str(status)))
+
+
+_LIB = None
+_DP = ctypes.POINTER(_dbl)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+
+_SIGS = {
+    "ssm_opts_default": (None, [ctypes.POINTER(ssm_opts)]),
+    "ssm_workspace_bytes": (_sz, [_i32, _i64, _i32, ctypes.POINTER(ssm_opts)]),
+    "ssm_create": (_i32, [_i32, _i64, _dbl, _dbl, _i32, _u64, ctypes.POINTER(ssm_opts), ctypes.POINTER(_vp)]),
+    "ssm_step": (_i32, [_vp]),
+    "ssm_run_steps": (_i32, [_vp, _i64]),
+    "ssm_run": (_i32, [_vp]),
+    "ssm_sync": (_i32, [_vp]),
+    "ssm_moments": (_i32, [_vp, _DP]),
+    "ssm_get_state": (_i32, [_vp, _DP, ctypes.POINTER(_i64)]),
+    "ssm_set_state": (_i32, [_vp, _DP, _i64]),
+    "ssm_get_stage": (_i32, [_vp, _i32, _DP]),
+    "ssm_stats": (_i32, [_vp, ctypes.POINTER(ssm_stats_t)]),
+    "ssm_destroy": (None, [_vp]),
+    "ssm_status_str": (ctypes.c_char_p, [_i32]),
+    "ssm_philox": (_i32, [_u64, _U32P, _i64, _U32P]),
+    "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
+    "ssm_cardano": (_i32, [_DP, _i64, _dbl, _DP]),
+    "ssm_pair_pass": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
+}
+
+
+def lib():
+    """Load libssm.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libssm.so is not built (%s); run paper_2105_09688_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status, where):
+    if status != SSM_OK:
+        raise SSMError(status, where)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def ssm_status_str(status):
+    return lib().ssm_status_str(int(status)).decode()
+
+
+def ssm_opts_default(**kw):
+    o = ssm_opts()
+    lib().ssm_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "coef_params":
+            for i, p in enumerate(v):
+                o.coef_params[i] = float(p)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def ssm_workspace_bytes(d, N, coef, opts=None):
+    return int(lib().ssm_workspace_bytes(int(d), int(N), int(coef), ctypes.byref(opts) if opts else None))
+
+
+def ssm_create(d, N, h, T, coef, seed, opts=None):
+    out = _vp()
+    _check(lib().ssm_create(int(d), int(N), float(h), float(T), int(coef), int(seed),
+                            ctypes.byref(opts) if opts else None, ctypes.byref(out)), "ssm_create")
+    return out
+
+
+def ssm_step(ctx):
+    _check(lib().ssm_step(ctx), "ssm_step")
+
+
+def ssm_run_steps(ctx, k):
+    _check(lib().ssm_run_steps(ctx, int(k)), "ssm_run_steps")
+
+
+def ssm_run(ctx):
+    _check(lib().ssm_run(ctx), "ssm_run")
+
+
+def ssm_sync(ctx):
+    _check(lib().ssm_sync(ctx), "ssm_sync")
+
+
+def ssm_moments(ctx, d):
+    out = np.empty((4, d))
+    _check(lib().ssm_moments(ctx, _dp(out)), "ssm_moments")
+    return out
+
+
+def ssm_get_state(ctx, N, d, out=None):
+    """Current state as an (N, d) array (or into ``out``, e.g. a pinned buffer) and step index."""
+    x = np.empty((N, d)) if out is None else out
+    n = _i64(0)
+    _check(lib().ssm_get_state(ctx, _dp(x), ctypes.byref(n)), "ssm_get_state")
+    return x, int(n.value)
+
+
+def ssm_set_state(ctx, x, n):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    _check(lib().ssm_set_state(ctx, _dp(x), int(n)), "ssm_set_state")
+
+
+def ssm_get_stage(ctx, which, N, d):
+    out = np.empty((N, d))
+    _check(lib().ssm_get_stage(ctx, int(which), _dp(out)), "ssm_get_stage")
+    return out
+
+
+def ssm_stats(ctx):
+    s = ssm_stats_t()
+    _check(lib().ssm_stats(ctx, ctypes.byref(s)), "ssm_stats")
+    return {"steps": s.steps, "newton_passes": s.newton_passes, "newton_rows": s.newton_rows,
+            "drift_rows": s.drift_rows, "fallbacks": s.fallbacks, "max_passes": s.max_passes,
+            "hist": [int(v) for v in s.hist]}
+
+
+def ssm_destroy(ctx):
+    if ctx:
+        lib().ssm_destroy(ctx)
+
+
+def ssm_philox(seed, ctr):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    _check(lib().ssm_philox(int(seed), ctr.ctypes.data_as(_U32P), ctr.shape[0], out.ctypes.data_as(_U32P)),
+           "ssm_philox")
+    return out
+
+
+def ssm_normals(seed, d, N, step, stream):
+    out = np.empty((int(N), int(d)))
+    _check(lib().ssm_normals(int(seed), int(d), int(N), int(step), int(stream), _dp(out)), "ssm_normals")
+    return out
+
+
+def ssm_pair_pass(ctx, which):
+    """Enqueue one full pair-sum pass (0: step-1 sums, 1: step-2 drift); returns the pair count."""
+    pairs = _i64(0)
+    _check(lib().ssm_pair_pass(ctx, int(which), ctypes.byref(pairs)), "ssm_pair_pass")
+    return int(pairs.value)
+
+
+def ssm_cardano(x, h):
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.empty_like(x)
+    _check(lib().ssm_cardano(_dp(x), x.size, float(h), _dp(y)), "ssm_cardano")
+    return y
+
+
+class SSM:
+    """A context whose device workspace is a torch tensor and whose stream is
+    torch's current CUDA stream (or one passed in).
+
+    >>> s = SSM(d=3, N=1 << 12, h=2**-8, T=1.0, coef=SSM_COEF_COUPLED3D, seed=2, precision=SSM_FP32C)
+    >>> s.run(); m = s.moments()
+    """
+
+    def __init__(self, d, N, h, T, coef, seed, stream=None, **opt):
+        import torch
+        self.d, self.N, self.h, self.T, self.coef = int(d), int(N), float(h), float(T), int(coef)
+        self.opts = ssm_opts_default(**opt)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.opts.stream = int(stream.cuda_stream) or None
+        nbytes = ssm_workspace_bytes(d, N, coef, self.opts)
+        if nbytes == 0:
+            raise SSMError(SSM_EINVAL, "ssm_workspace_bytes")
+        # 256-byte aligned device workspace owned by torch's allocator
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        self.opts.workspace = (base + 255) // 256 * 256
+        self.opts.workspace_bytes = nbytes
+        self.ctx = ssm_create(d, N, h, T, coef, seed, self.opts)
+
+    def step(self):
+        ssm_step(self.ctx)
+
+    def run_steps(self, k):
+        ssm_run_steps(self.ctx, k)
+
+    def run(self):
+        ssm_run(self.ctx)
+
+    def sync(self):
+        ssm_sync(self.ctx)
+
+    def moments(self):
+        return ssm_moments(self.ctx, self.d)
+
+    def get_state(self, out=None):
+        return ssm_get_state(self.ctx, self.N, self.d, out)
+
+    def set_state(self, x, n):
+        ssm_set_state(self.ctx, x, n)
+
+    def get_stage(self, which):
+        return ssm_get_stage(self.ctx, which, self.N, self.d)
+
+    def stats(self):
+        return ssm_stats(self.ctx)
+
+    def pair_pass(self, which):
+        return ssm_pair_pass(self.ctx, which)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ssm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

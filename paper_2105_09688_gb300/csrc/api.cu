@@ -1,0 +1,509 @@
+// api.cu -- the C ABI declared in include/ssm.h: context life cycle, the launch
+// sequence of one SSM step (§2.3, eq. SSTM:scheme 1 and SSTM:scheme 2), CUDA-graph
+// replay of whole runs, state transfer and the component entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ssm.h"
+#include "ssm_device.cuh"
+
+namespace ssm {
+cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
+                      const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st);
+bool pair_shape_supported(int threads, int rpt);
+cudaError_t launch_init_x0(ssm_ctx *c);
+cudaError_t launch_moments(ssm_ctx *c);
+cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st);
+cudaError_t launch_ou_implicit(ssm_ctx *c);
+cudaError_t launch_newton_begin(ssm_ctx *c);
+cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32);
+cudaError_t launch_step_stats(ssm_ctx *c);
+cudaError_t launch_euler(ssm_ctx *c, double bscale);
+cudaError_t launch_set_step(ssm_ctx *c, long long n);
+cudaError_t launch_aos_to_soa(const double *a, double *s, int d, int64_t N, int64_t Np, cudaStream_t st);
+cudaError_t launch_soa_to_aos(const double *s, double *a, int d, int64_t N, int64_t Np, cudaStream_t st);
+cudaError_t launch_stage_b(ssm_ctx *c, double bscale);
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, double *out, cudaStream_t st);
+cudaError_t ws_forward_start(ssm_ctx *c);
+}  // namespace ssm
+
+using namespace ssm;
+
+namespace {
+
+constexpr int64_t N_MAX = (int64_t)1 << 26;
+
+bool fp32_pairs(const ssm_ctx *c) { return c->prec != SSM_FP64; }
+
+// Coordinate scale of the FP32 Gaussian kernels and the factor that turns the
+// drift partial sums into b: b = coef * (1/N) * sum / scale.
+void drift_scale(int coef, bool fp32, int64_t N, double *scale, double *bscale) {
+    const double cexp = coef == SSM_COEF_CUBIC1D_GAUSS ? 1.0 : 0.5;   // exp(-cexp r^2)
+    const double cb = coef == SSM_COEF_CUBIC1D_GAUSS ? 0.5 : 1.0;     // coefficient of the integral
+    *scale = fp32 ? sqrt(cexp * LOG2E) : 1.0;
+    *bscale = cb / ((double)N * *scale);
+}
+
+// Launch shape of a pair kind: threads x targets-per-thread tiles over the
+// targets, the sources split into chunks so that the grid fills the GPU with
+// several waves of blocks.
+Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
+    Plan p;
+    p.threads = 128;
+    p.rpt = fp32 ? (kind == PK_DRIFT1 ? 8 : 4) : 2;
+    const int64_t tiles = (N + p.threads * p.rpt - 1) / (p.threads * p.rpt);
+    const int64_t max_chunks = (N + SUB - 1) / SUB;
+    int64_t chunks = force_chunks > 0 ? force_chunks : (2432 + tiles - 1) / tiles;   // ~16 blocks per SM
+    if (chunks < 1) chunks = 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks > 65535) chunks = 65535;
+    int64_t len = (N + chunks - 1) / chunks;
+    len = (len + SUB - 1) / SUB * SUB;
+    p.chunk_len = len;
+    p.chunks = (int)((N + len - 1) / len);
+    return p;
+}
+
+struct Layout {
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, total;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int64_t padded(int64_t N) { return (N + 127) / 128 * 128; }
+
+Layout make_layout(int d, int64_t N, int coef, const Plan &pn, const Plan &pd, int kmax) {
+    Layout L;
+    const int64_t Np = padded(N);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.x = take(sizeof(double) * d * Np);
+    L.y = take(sizeof(double) * d * Np);
+    L.stage = take(sizeof(double) * d * Np);
+    size_t part = 0;
+    if (coef == SSM_COEF_COUPLED3D) {
+        part = (size_t)pn.chunks * 4;
+        if ((size_t)pd.chunks * 3 > part) part = (size_t)pd.chunks * 3;
+    } else if (coef == SSM_COEF_CUBIC1D_GAUSS) {
+        part = (size_t)pd.chunks;
+    }
+    L.part = take(sizeof(double) * part * Np);
+    L.mpart = take(sizeof(double) * RED_BLOCKS * 12);
+    L.mom = take(sizeof(double) * 12);
+    L.ymean = take(sizeof(double) * 4);
+    const bool nt = coef == SSM_COEF_COUPLED3D;
+    L.act0 = take(nt ? sizeof(int) * Np : 0);
+    L.act1 = take(nt ? sizeof(int) * Np : 0);
+    L.cnt = take(sizeof(int) * (kmax + 2));
+    L.passes = take(nt ? sizeof(int) * Np : 0);
+    L.err = take(sizeof(int));
+    L.ticket = take(sizeof(unsigned));
+    L.dstep = take(sizeof(long long));
+    L.counters = take(sizeof(long long) * CNT_N);
+    L.hist = take(sizeof(long long) * 16);
+    L.wsw = take(nt ? 65536 * sizeof(float) : 0);
+    L.total = o;
+    return L;
+}
+
+void fill_defaults(ssm_opts *o) {
+    memset(o, 0, sizeof *o);
+    o->precision = SSM_FP64;
+    o->newton_tol = 0.0;   // 0 = per-precision default
+    o->newton_kmax = 12;
+    o->fine_log2 = 0;
+    o->x0_mean = 0.0;
+    o->x0_std = 1.0;
+    o->ws_passes = 3;
+}
+
+ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_opts &o) {
+    if (N < 1 || N > N_MAX || !(h > 0.0) || !(T > 0.0) || !(h <= T)) return SSM_EINVAL;
+    if (o.precision < SSM_FP64 || o.precision > SSM_FP32C_LEARNED) return SSM_EINVAL;
+    if (o.newton_kmax < 1 || o.newton_kmax > 64) return SSM_EINVAL;
+    double Lv;
+    if (coef == SSM_COEF_CUBIC1D_GAUSS) {
+        if (d != 1) return SSM_EINVAL;
+        Lv = 1.0;
+    } else if (coef == SSM_COEF_COUPLED3D) {
+        if (d != 3) return SSM_EINVAL;
+        Lv = 1.0 / 16.0;
+    } else if (coef == SSM_COEF_OU) {
+        if (d < 1 || d > 3) return SSM_EINVAL;
+        if (o.precision != SSM_FP64) return SSM_EINVAL;
+        Lv = o.coef_params[0];
+    } else {
+        return SSM_EINVAL;
+    }
+    if (o.precision == SSM_FP32C_LEARNED && coef != SSM_COEF_COUPLED3D) return SSM_EINVAL;
+    // Theorem 2.3: h <= 1/(1 + 2 L_v) when L_v > -1/2; also 1 - h L_v > 0 for Lemma 4.1.
+    if (Lv > -0.5 && h > 1.0 / (1.0 + 2.0 * Lv)) return SSM_EINVAL;
+    const double M = T / h;
+    const double Mr = nearbyint(M);
+    if (Mr < 1.0 || fabs(Mr * h - T) > 1e-12 * T) return SSM_EINVAL;
+    if (o.fine_log2 < 0 || o.fine_log2 > 30) return SSM_EINVAL;
+    if (o.fine_log2 > 0) {
+        const double hf = T / (double)(1ll << o.fine_log2);
+        const double r = h / hf;
+        if (r < 1.0 || fabs(nearbyint(r) - r) > 1e-9) return SSM_EINVAL;
+    }
+    if (o.tile_chunks < 0) return SSM_EINVAL;
+    return SSM_OK;
+}
+
+ssm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SSM_OK;
+    if (e == cudaErrorMemoryAllocation) return SSM_ENOMEM;
+    return SSM_ECUDA;
+}
+
+// Read the device error word and fold it into the sticky status.
+ssm_status harvest(ssm_ctx *c) {
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    int e = 0;
+    cudaError_t ce = cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) { c->status = SSM_ECUDA; return SSM_ECUDA; }
+    if (e & ERR_NONFINITE) c->status = SSM_ENONFINITE;
+    else if (e & ERR_NOCONV) c->status = SSM_ENOCONV;
+    else if (e & ERR_TIMEOUT) c->status = SSM_ETIMEOUT;
+    return (ssm_status)c->status;
+}
+
+// Enqueue one SSM step (no host synchronisation, safe to capture in a graph).
+cudaError_t enqueue_step(ssm_ctx *c) {
+    cudaError_t e = cudaSuccess;
+    const bool f32 = fp32_pairs(c);
+    double scale, bscale;
+    drift_scale(c->coef, f32, c->N, &scale, &bscale);
+    if (c->coef == SSM_COEF_CUBIC1D_GAUSS) {
+        // step 1: closed-form root per particle
+        if ((e = launch_cardano(c->x, c->y, c->N, c->h, c->st)) != cudaSuccess) return e;
+        // step 2: b(Y_i, mu^Y) pair sums, then the fused update
+        if ((e = pair_sums(PK_DRIFT1, f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale, c->part,
+                           c->st)) != cudaSuccess)
+            return e;
+        return launch_euler(c, bscale);
+    }
+    if (c->coef == SSM_COEF_OU) {
+        if ((e = launch_ou_implicit(c)) != cudaSuccess) return e;
+        return launch_euler(c, 0.0);
+    }
+    // SSM_COEF_COUPLED3D
+    if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
+    if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
+        if ((e = ws_forward_start(c)) != cudaSuccess) return e;
+    int *a_in = c->act0, *a_out = c->act1;
+    for (int k = 0; k < c->kmax; ++k) {
+        if ((e = pair_sums(PK_NEWTON3, f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0, c->part,
+                           c->st)) != cudaSuccess)
+            return e;
+        if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
+        int *t = a_in; a_in = a_out; a_out = t;
+    }
+    if ((e = launch_step_stats(c)) != cudaSuccess) return e;
+    if ((e = pair_sums(PK_DRIFT3, f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale, c->part,
+                       c->st)) != cudaSuccess)
+        return e;
+    return launch_euler(c, bscale);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ssm_opts_default(ssm_opts *opts) {
+    if (opts) fill_defaults(opts);
+}
+
+size_t ssm_workspace_bytes(int d, int64_t N, int coef, const ssm_opts *opts) {
+    ssm_opts o;
+    if (opts) o = *opts; else fill_defaults(&o);
+    if (N < 1 || N > N_MAX || d < 1 || d > 3) return 0;
+    const bool f32 = o.precision != SSM_FP64;
+    Plan pn = make_plan(N, f32, PK_NEWTON3, o.tile_chunks);
+    Plan pd = make_plan(N, f32, coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, o.tile_chunks);
+    return make_layout(d, N, coef, pn, pd, o.newton_kmax).total;
+}
+
+ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t seed, const ssm_opts *opts,
+                      ssm_ctx **out) {
+    if (!out) return SSM_EINVAL;
+    *out = nullptr;
+    ssm_opts o;
+    if (opts) o = *opts; else fill_defaults(&o);
+    if (o.newton_kmax == 0) o.newton_kmax = 12;
+    if (o.ws_passes <= 0) o.ws_passes = 3;
+    ssm_status s = check_args(d, N, h, T, coef, o);
+    if (s != SSM_OK) return s;
+
+    ssm_ctx *c = new (std::nothrow) ssm_ctx();
+    if (!c) return SSM_ENOMEM;
+    c->d = d; c->coef = coef; c->prec = o.precision; c->N = N; c->Np = padded(N);
+    c->h = h; c->T = T; c->seed = seed; c->opt = o;
+    c->M = (int64_t)nearbyint(T / h);
+    c->n = 0;
+    c->kmax = o.newton_kmax;
+    c->tol = o.newton_tol > 0.0 ? o.newton_tol : (o.precision == SSM_FP64 ? 1e-13 : 1e-10);
+    const bool f32 = o.precision != SSM_FP64;
+    c->plan_newton = make_plan(N, f32, PK_NEWTON3, o.tile_chunks);
+    c->plan_drift = make_plan(N, f32, coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, o.tile_chunks);
+    Layout L = make_layout(d, N, coef, c->plan_newton, c->plan_drift, c->kmax);
+
+    cudaError_t e = cudaSuccess;
+    if (o.stream) {
+        c->st = (cudaStream_t)o.stream;
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return cuda_status(e); }
+        c->own_stream = true;
+    }
+    if (o.workspace) {
+        if (o.workspace_bytes < L.total || ((uintptr_t)o.workspace & 255u)) {
+            if (c->own_stream) cudaStreamDestroy(c->st);
+            delete c;
+            return o.workspace_bytes < L.total ? SSM_ENOMEM : SSM_EINVAL;
+        }
+        c->ws = (char *)o.workspace;
+        c->own_ws = false;
+    } else {
+        e = cudaMalloc((void **)&c->ws, L.total);
+        if (e != cudaSuccess) {
+            if (c->own_stream) cudaStreamDestroy(c->st);
+            delete c;
+            return cuda_status(e);
+        }
+        c->own_ws = true;
+    }
+    c->ws_bytes = L.total;
+    char *b = c->ws;
+    c->x = (double *)(b + L.x); c->y = (double *)(b + L.y); c->stage = (double *)(b + L.stage);
+    c->part = (double *)(b + L.part); c->mpart = (double *)(b + L.mpart); c->mom = (double *)(b + L.mom);
+    c->ymean = (double *)(b + L.ymean);
+    c->act0 = (int *)(b + L.act0); c->act1 = (int *)(b + L.act1); c->cnt = (int *)(b + L.cnt);
+    c->passes = (int *)(b + L.passes); c->err = (int *)(b + L.err); c->ticket = (unsigned *)(b + L.ticket);
+    c->dstep = (long long *)(b + L.dstep); c->counters = (long long *)(b + L.counters);
+    c->hist = (long long *)(b + L.hist);
+    c->ws_w = (float *)(b + L.wsw);
+    c->ws_loaded = 0;
+
+    // zero everything (padding lanes of the SoA arrays included), then draw X_0
+    e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
+    if (e == cudaSuccess) e = launch_init_x0(c);
+    if (e != cudaSuccess) {
+        ssm_destroy(c);
+        return cuda_status(e);
+    }
+    *out = c;
+    return SSM_OK;
+}
+
+ssm_status ssm_step(ssm_ctx *c) {
+    if (!c) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    if (c->n >= c->M) return SSM_ESTATE;
+    cudaError_t e = enqueue_step(c);
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    c->n += 1;
+    return SSM_OK;
+}
+
+ssm_status ssm_run_steps(ssm_ctx *c, int64_t k) {
+    if (!c || k < 0) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    if (c->n + k > c->M) return SSM_ESTATE;
+    if (k == 0) return SSM_OK;
+    cudaError_t e = cudaSuccess;
+    if (!c->graph_ready) {
+        cudaGraph_t g;
+        e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = enqueue_step(c);
+            e = cudaStreamEndCapture(c->st, &g);
+            if (e1 != cudaSuccess) e = e1;
+            if (e == cudaSuccess) {
+                e = cudaGraphInstantiate(&c->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e == cudaSuccess) c->graph_ready = true;
+            }
+        }
+        if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    }
+    for (int64_t s = 0; s < k; ++s) {
+        e = cudaGraphLaunch(c->gexec, c->st);
+        if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    }
+    c->n += k;
+    return SSM_OK;
+}
+
+ssm_status ssm_run(ssm_ctx *c) {
+    if (!c) return SSM_EINVAL;
+    return ssm_run_steps(c, c->M - c->n);
+}
+
+ssm_status ssm_sync(ssm_ctx *c) {
+    if (!c) return SSM_EINVAL;
+    return harvest(c);
+}
+
+ssm_status ssm_moments(ssm_ctx *c, double *out) {
+    if (!c || !out) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    cudaError_t e = cudaMemcpyAsync(out, c->mom, sizeof(double) * 4 * c->d, cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    return harvest(c);
+}
+
+ssm_status ssm_get_state(ssm_ctx *c, double *x, int64_t *n) {
+    if (!c) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    if (x) {
+        cudaError_t e = launch_soa_to_aos(c->x, c->stage, c->d, c->N, c->Np, c->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(x, c->stage, sizeof(double) * c->d * c->N, cudaMemcpyDeviceToHost, c->st);
+        if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    }
+    if (n) *n = c->n;
+    return harvest(c);
+}
+
+ssm_status ssm_set_state(ssm_ctx *c, const double *x, int64_t n) {
+    if (!c || !x || n < 0 || n > c->M) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    cudaError_t e = cudaMemcpyAsync(c->stage, x, sizeof(double) * c->d * c->N, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = launch_aos_to_soa(c->stage, c->x, c->d, c->N, c->Np, c->st);
+    if (e == cudaSuccess) e = launch_set_step(c, n);
+    if (e == cudaSuccess) e = launch_moments(c);
+    // the caller's array may be reused once this returns
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    c->n = n;
+    return SSM_OK;
+}
+
+ssm_status ssm_get_stage(ssm_ctx *c, int which, double *out) {
+    if (!c || !out || (which != SSM_STAGE_Y && which != SSM_STAGE_B)) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    cudaError_t e;
+    if (which == SSM_STAGE_Y) {
+        e = launch_soa_to_aos(c->y, c->stage, c->d, c->N, c->Np, c->st);
+    } else {
+        double scale, bscale;
+        drift_scale(c->coef, fp32_pairs(c), c->N, &scale, &bscale);
+        e = launch_stage_b(c, bscale);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->stage, sizeof(double) * c->d * c->N, cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    return harvest(c);
+}
+
+ssm_status ssm_stats(ssm_ctx *c, ssm_stats_t *out) {
+    if (!c || !out) return SSM_EINVAL;
+    long long cn[CNT_N], hs[16];
+    cudaError_t e = cudaMemcpyAsync(cn, c->counters, sizeof cn, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, c->hist, sizeof hs, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    memset(out, 0, sizeof *out);
+    out->steps = cn[CNT_STEPS];
+    out->newton_passes = cn[CNT_NEWTON_PASSES];
+    out->newton_rows = cn[CNT_NEWTON_ROWS];
+    out->drift_rows = cn[CNT_DRIFT_ROWS];
+    out->fallbacks = cn[CNT_FALLBACKS];
+    out->max_passes = cn[CNT_MAX_PASSES];
+    for (int k = 0; k < 16; ++k) out->hist[k] = hs[k];
+    return harvest(c);
+}
+
+void ssm_destroy(ssm_ctx *c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+const char *ssm_status_str(int s) {
+    switch (s) {
+    case SSM_OK: return "SSM_OK";
+    case SSM_EINVAL: return "SSM_EINVAL: invalid argument";
+    case SSM_ENOMEM: return "SSM_ENOMEM: out of device memory or workspace too small";
+    case SSM_ECUDA: return "SSM_ECUDA: CUDA runtime error";
+    case SSM_ENOCONV: return "SSM_ENOCONV: implicit step did not reach its tolerance";
+    case SSM_ENONFINITE: return "SSM_ENONFINITE: non-finite particle state";
+    case SSM_ETIMEOUT: return "SSM_ETIMEOUT: bounded device wait gave up";
+    case SSM_ESTATE: return "SSM_ESTATE: call not valid in the current state";
+    }
+    return "unknown ssm_status";
+}
+
+// ---- component entry points ------------------------------------------------
+
+ssm_status ssm_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out) {
+    if (!ctr || !out || n < 0 || n > N_MAX) return SSM_EINVAL;
+    if (n == 0) return SSM_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dc, sizeof(uint32_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dout, sizeof(uint32_t) * 4 * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(seed, dc, n, dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    return cuda_status(e);
+}
+
+ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream, double *out) {
+    if (!out || d < 1 || d > 3 || N < 0 || N > N_MAX || step < 0 || step > 0xffffffffll || stream < 0) return SSM_EINVAL;
+    if (N == 0) return SSM_OK;
+    double *dz = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dz, sizeof(double) * d * N);
+    if (e == cudaSuccess) e = launch_normals(seed, d, N, (uint32_t)step, (uint32_t)stream, dz, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dz, sizeof(double) * d * N, cudaMemcpyDeviceToHost);
+    cudaFree(dz);
+    return cuda_status(e);
+}
+
+ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
+    if (!c || (which != 0 && which != 1)) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    if (c->coef == SSM_COEF_OU || (which == 0 && c->coef != SSM_COEF_COUPLED3D)) return SSM_EINVAL;
+    const bool f32 = fp32_pairs(c);
+    cudaError_t e;
+    if (which == 0) {
+        e = pair_sums(PK_NEWTON3, f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0, c->part, c->st);
+    } else {
+        double scale, bscale;
+        drift_scale(c->coef, f32, c->N, &scale, &bscale);
+        e = pair_sums(c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, f32, c->plan_drift, c->y, c->y,
+                      nullptr, nullptr, c->N, c->Np, scale, c->part, c->st);
+    }
+    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+    if (pairs) *pairs = c->N * c->N;
+    return SSM_OK;
+}
+
+ssm_status ssm_cardano(const double *x, int64_t n, double h, double *y) {
+    if (!x || !y || n < 0 || n > N_MAX || !(h > 0.0) || !(h < 1.0 / 3.0 + 1e-15)) return SSM_EINVAL;
+    if (n == 0) return SSM_OK;
+    double *dx = nullptr, *dy = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dx, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dy, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_cardano(dx, dy, n, h, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dy);
+    return cuda_status(e);
+}
+
+}  // extern "C"

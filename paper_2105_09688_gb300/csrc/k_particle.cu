@@ -1,0 +1,528 @@
+// k_particle.cu -- the O(N) kernels of the split-step method: initial state,
+// the per-particle parts of step 1 (Cardano closed form, the Newton-type update
+// that consumes the pair sums, the linear OU solve), and step 2 fused with the
+// Brownian increments and the FP64 moment reduction.
+//
+// References are to Chen & dos Reis, arXiv:2105.09688: §2.3 (eq. SSTM:scheme 1
+// and SSTM:scheme 2), Lemma 4.1 (unique root of the implicit map), §3.4.1
+// (the OU example).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssm_device.cuh"
+
+namespace ssm {
+
+// ---------------------------------------------------------------------------
+// Block reduction of NV doubles per thread into out[NV] (thread 0 writes).
+// ---------------------------------------------------------------------------
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double *v, double *out) {
+    __shared__ double sh[THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) s += sh[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// True in exactly one block: the last to finish (its view of the other blocks'
+// partials is complete).  Resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) *ticket = 0u;
+    return is_last;
+}
+
+// Moments (1/N) sum_i x^k, k = 1..4, for D components: per-block partials in
+// mpart[block][4*D], reduced in block order by the last block into mom[4*D].
+template <int D>
+__device__ __forceinline__ void moments_epilogue(double (&m)[4 * D], int64_t N, double *mpart, unsigned *ticket,
+                                                 double *mom, int *err) {
+    __shared__ double bsum[4 * D];
+    block_sum<4 * D, EUL_THREADS>(m, bsum);
+    __syncthreads();
+    if (threadIdx.x < 4 * D) mpart[(int64_t)blockIdx.x * 4 * D + threadIdx.x] = bsum[threadIdx.x];
+    if (last_block(ticket)) {
+        if (threadIdx.x < 4 * D) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&mpart[(int64_t)b * 4 * D + threadIdx.x]);
+            const double v = s / (double)N;
+            mom[threadIdx.x] = v;
+            if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
+        }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void add_powers(double (&m)[4 * D], int c, double v) {
+    const double v2 = v * v;
+    m[0 * D + c] += v;
+    m[1 * D + c] += v2;
+    m[2 * D + c] += v2 * v;
+    m[3 * D + c] += v2 * v2;
+}
+
+// X_0^i = mean + std Z^i, Z from Philox stream 0 at step 0 (and its moments).
+template <int D>
+__global__ void __launch_bounds__(EUL_THREADS)
+k_init_x0(double *x, int64_t N, int64_t Np, uint64_t seed, double mean, double sd, double *mpart,
+          unsigned *ticket, double *mom, int *err) {
+    double m[4 * D];
+#pragma unroll
+    for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double z[3];
+        normals<D>(seed, (uint32_t)i, 0u, 0u, z);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double v = mean + sd * z[c];
+            x[c * Np + i] = v;
+            add_powers<D>(m, c, v);
+        }
+    }
+    moments_epilogue<D>(m, N, mpart, ticket, mom, err);
+}
+
+template <int D>
+__global__ void __launch_bounds__(EUL_THREADS)
+k_moments(const double *x, int64_t N, int64_t Np, double *mpart, unsigned *ticket, double *mom, int *err) {
+    double m[4 * D];
+#pragma unroll
+    for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < D; ++c) add_powers<D>(m, c, x[c * Np + i]);
+    moments_epilogue<D>(m, N, mpart, ticket, mom, err);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1, SSM_COEF_CUBIC1D_GAUSS: the real root of h y^3 + (1-h) y - x = 0.
+// Depressed cubic y^3 + p y + q = 0, p = (1-h)/h > 0, q = -x/h: one real root.
+// With y = u + w, u w = -p/3 and u^3 + w^3 = -q, the root equals
+// -q / (u^2 + p/3 + w^2), a quotient of positive sums that keeps full relative
+// accuracy for small |x|.  One Newton correction follows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cardano_root(double x, double h) {
+    if (x == 0.0) return 0.0;
+    const double p = (1.0 - h) / h, q = -x / h;
+    const double p3 = p / 3.0;
+    const double disc = 0.25 * q * q + p3 * p3 * p3;
+    double u = cbrt(0.5 * fabs(q) + sqrt(disc));
+    if (q > 0.0) u = -u;
+    const double w = -p3 / u;
+    const double y = -q / (u * u + p3 + w * w);
+    const double f = h * y * y * y + (1.0 - h) * y - x;
+    const double fp = 3.0 * h * y * y + (1.0 - h);
+    return y - f / fp;
+}
+
+__global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, int64_t n, double h) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = cardano_root(x[i], h);
+}
+
+// Step 1, SSM_COEF_OU (v = rho x): Y = X / (1 - h rho) (Remark 4.3), and the mean
+// of Y that step 2's b = lambda * mean needs.
+template <int D>
+__global__ void __launch_bounds__(EUL_THREADS)
+k_ou_implicit(const double *x, double *y, int64_t N, int64_t Np, double inv, double *mpart, unsigned *ticket,
+              double *ymean) {
+    double m[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) m[c] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double v = x[c * Np + i] / inv;
+            y[c * Np + i] = v;
+            m[c] += v;
+        }
+    __shared__ double bsum[D];
+    block_sum<D, EUL_THREADS>(m, bsum);
+    __syncthreads();
+    if (threadIdx.x < D) mpart[(int64_t)blockIdx.x * D + threadIdx.x] = bsum[threadIdx.x];
+    if (last_block(ticket) && threadIdx.x < D) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&mpart[(int64_t)b * D + threadIdx.x]);
+        ymean[threadIdx.x] = s / (double)N;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 1, SSM_COEF_COUPLED3D.  The implicit equation
+//   F(Y) = Y - X - h ( -Y|Y|^2 + 0.5 S(Y) ) = 0,  S(Y) = (1/N) sum_j (X_j - Y) w_j,
+//   w_j = 1 / (1 + |X_j - Y|^2)
+// is solved for all particles at once in passes.  Each pass evaluates S and
+// Sw = (1/N) sum_j w_j at the current Y of every unconverged particle (the
+// O(N^2) pair kernel), then this kernel forms the residual in double; a
+// particle whose max-norm residual is within tol is done.  Otherwise Y moves to
+// the root of the local model
+//   u = X + h ( -u|u|^2 + 0.5 ( S - Sw (u - Y) ) ),
+// whose cubic part is exact and whose pair part is S linearised with the
+// diagonal -Sw I of its Jacobian (1/N) sum_j (-w_j I + 2 w_j^2 d_j d_j^T).  That
+// local problem has the Jacobian a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw), which
+// Sherman-Morrison inverts in closed form; a few Newton steps solve it to
+// rounding.  The outer iteration contracts by about 0.5 h |(2 w^2 d d^T)| per pass.
+// ---------------------------------------------------------------------------
+__global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
+                               int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
+                               int64_t N, int64_t Np) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[c * Np + i] = x[c * Np + i];
+        act[i] = (int)i;
+        passes[i] = 0;
+    }
+    if (i == 0) {
+        cnt[0] = (int)N;
+        for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
+        for (int k = 0; k < 16; ++k) hist[k] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int *__restrict__ act_in,
+                const int *__restrict__ cnt_in, int *__restrict__ act_out, int *__restrict__ cnt_out,
+                const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h, double tol,
+                int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err) {
+    __shared__ int bh[16];
+    if (threadIdx.x < 16) bh[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_in = *cnt_in;
+    bool keep = false;
+    int i = 0;
+    if (t < n_in) {
+        i = act_in[t];
+        double S[3] = { 0.0, 0.0, 0.0 }, Sw = 0.0;
+        for (int k = 0; k < chunks; ++k) {
+            const double *pk = part + (int64_t)k * 4 * Np + t;
+            S[0] += pk[0];
+            S[1] += pk[Np];
+            S[2] += pk[2 * Np];
+            Sw += pk[3 * Np];
+        }
+        const double invN = 1.0 / (double)N;
+        double Y[3], X[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S[c] *= invN;
+            Y[c] = y[c * Np + i];
+            X[c] = x[c * Np + i];
+        }
+        Sw *= invN;
+        if (fp32_targets) {
+            // The pair kernel evaluated the numerators at the FP32 rounding of Y;
+            // (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y)) corrects them exactly.
+#pragma unroll
+            for (int c = 0; c < 3; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
+        }
+        const double yy = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+        double rinf = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
+            rinf = fmax(rinf, fabs(r));
+            if (r != r) rinf = r;   // NaN propagates as "not converged"
+        }
+        if (rinf <= tol) {
+            passes[i] = pass + 1;
+            atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
+        } else if (pass + 1 >= kmax || !(rinf == rinf)) {
+            passes[i] = pass + 1;
+            atomicOr(err, rinf == rinf ? ERR_NOCONV : ERR_NONFINITE);
+        } else {
+            double u[3] = { Y[0], Y[1], Y[2] };
+            for (int it = 0; it < 30; ++it) {
+                const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                double g[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * (u[c] - Y[c]);
+                const double a = 1.0 + h * uu + 0.5 * h * Sw;
+                const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+                const double f = 2.0 * h * ug / (a + 2.0 * h * uu);
+                double smax = 0.0, umax = 1.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double s = (g[c] - f * u[c]) / a;
+                    u[c] -= s;
+                    smax = fmax(smax, fabs(s));
+                    umax = fmax(umax, fabs(u[c]));
+                }
+                if (smax <= 1e-16 * umax) break;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[c * Np + i] = u[c];
+            keep = true;
+        }
+    }
+    // warp-aggregated append of the particles that stay active
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(cnt_out, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) act_out[base + __popc(m & ((1u << lane) - 1u))] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 && bh[threadIdx.x]) atomicAdd((unsigned long long *)&hist[threadIdx.x], (unsigned long long)bh[threadIdx.x]);
+}
+
+// Work counters of one implicit step (one thread).
+__global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *counters) {
+    long long rows = 0, npass = 0;
+    for (int k = 0; k < kmax; ++k) {
+        rows += cnt[k];
+        if (cnt[k] > 0) npass = k + 1;
+    }
+    counters[CNT_NEWTON_ROWS] += rows;
+    counters[CNT_NEWTON_PASSES] += npass;
+    if (npass > counters[CNT_MAX_PASSES]) counters[CNT_MAX_PASSES] = npass;
+}
+
+// ---------------------------------------------------------------------------
+// Step 2 (eq. SSTM:scheme 2) fused with the Brownian increment and the moments
+// of the new state:  X'_i = Y_i + h b(Y_i, mu^Y) + sigma(Y_i) dW_n^i.
+// b comes from the pair partials (bscale folds in 1/N, the coefficient and the
+// FP32 coordinate scale) or, for OU, from lambda * mean(Y).  dW is drawn on the
+// step's own grid (fine_r = 1) or summed over fine_r increments of the finer
+// grid, so that runs at different h share one Brownian path.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(EUL_THREADS)
+k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
+        double bscale, int coef, double lam, double eta, const double *__restrict__ ymean, int64_t N, int64_t Np,
+        double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep, double *mpart,
+        unsigned *ticket, double *mom, int *err, long long *counters) {
+    const long long n = *dstep;
+    double m[4 * D];
+#pragma unroll
+    for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double yv[D], b[D], dw[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            yv[c] = y[c * Np + i];
+            if (coef == SSM_COEF_OU) {
+                b[c] = lam * ymean[c];
+            } else {
+                double s = 0.0;
+                for (int k = 0; k < chunks; ++k) s += part[((int64_t)k * D + c) * Np + i];
+                b[c] = s * bscale;
+            }
+        }
+        if (fine_r <= 1) {
+            double z[3];
+            normals<D>(seed, (uint32_t)i, (uint32_t)n, 1u, z);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dw[c] = sqrt_h * z[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) dw[c] = 0.0;
+            for (int r = 0; r < fine_r; ++r) {
+                double z[3];
+                normals<D>(seed, (uint32_t)i, (uint32_t)(n * fine_r + r), 1u, z);
+#pragma unroll
+                for (int c = 0; c < D; ++c) dw[c] += sqrt_hf * z[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            double sig;
+            if (coef == SSM_COEF_CUBIC1D_GAUSS) sig = 0.4 * yv[c] + 0.1;
+            else if (coef == SSM_COEF_COUPLED3D) sig = 0.3 * yv[c] + 0.2;
+            else sig = eta;
+            const double xn = yv[c] + h * b[c] + sig * dw[c];
+            x[c * Np + i] = xn;
+            add_powers<D>(m, c, xn);
+        }
+    }
+    moments_epilogue<D>(m, N, mpart, ticket, mom, err);
+}
+
+// The step index advances in a separate one-thread kernel after k_euler, so no
+// block of k_euler can observe the new value.
+__global__ void k_advance(long long *dstep, long long *counters, long long N) {
+    *dstep += 1;
+    counters[CNT_STEPS] += 1;
+    counters[CNT_DRIFT_ROWS] += N;
+}
+
+__global__ void k_set_step(long long *dstep, long long n) { *dstep = n; }
+
+// Host particle-major <-> device SoA.
+__global__ void k_aos_to_soa(const double *__restrict__ a, double *__restrict__ s, int d, int64_t N, int64_t Np) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N * d; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / d;
+        const int c = (int)(k - i * d);
+        s[c * Np + i] = a[k];
+    }
+}
+__global__ void k_soa_to_aos(const double *__restrict__ s, double *__restrict__ a, int d, int64_t N, int64_t Np) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N * d; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / d;
+        const int c = (int)(k - i * d);
+        a[k] = s[c * Np + i];
+    }
+}
+// b of the last step, particle-major, from the drift partials.
+__global__ void k_stage_b(const double *__restrict__ part, int chunks, double bscale, int coef, double lam,
+                          const double *__restrict__ ymean, double *__restrict__ a, int d, int64_t N, int64_t Np) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N * d; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / d;
+        const int c = (int)(k - i * d);
+        if (coef == SSM_COEF_OU) {
+            a[k] = lam * ymean[c];
+        } else {
+            double s = 0.0;
+            for (int q = 0; q < chunks; ++q) s += part[((int64_t)q * d + c) * Np + i];
+            a[k] = s * bscale;
+        }
+    }
+}
+
+// Component kernels behind ssm_philox / ssm_normals / ssm_cardano.
+__global__ void k_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const U4 w = philox10(U4{ ctr[4 * k], ctr[4 * k + 1], ctr[4 * k + 2], ctr[4 * k + 3] }, (uint32_t)seed,
+                              (uint32_t)(seed >> 32));
+        out[4 * k] = w.a;
+        out[4 * k + 1] = w.b;
+        out[4 * k + 2] = w.c;
+        out[4 * k + 3] = w.d;
+    }
+}
+template <int D>
+__global__ void k_normals(uint64_t seed, int64_t N, uint32_t step, uint32_t stream, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double z[3];
+        normals<D>(seed, (uint32_t)i, step, stream, z);
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[i * D + c] = z[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (enqueue only).
+// ---------------------------------------------------------------------------
+static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+static inline unsigned gs_blocks(int64_t n, int th) {   // grid-stride launch size
+    const int64_t b = (n + th - 1) / th;
+    return (unsigned)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+}
+
+cudaError_t launch_init_x0(ssm_ctx *c) {
+    if (c->d == 1)
+        k_init_x0<1><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->seed, c->opt.x0_mean, c->opt.x0_std,
+                                                           c->mpart, c->ticket, c->mom, c->err);
+    else if (c->d == 2)
+        k_init_x0<2><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->seed, c->opt.x0_mean, c->opt.x0_std,
+                                                           c->mpart, c->ticket, c->mom, c->err);
+    else
+        k_init_x0<3><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->seed, c->opt.x0_mean, c->opt.x0_std,
+                                                           c->mpart, c->ticket, c->mom, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(ssm_ctx *c) {
+    if (c->d == 1) k_moments<1><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->mpart, c->ticket, c->mom, c->err);
+    else if (c->d == 2) k_moments<2><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->mpart, c->ticket, c->mom, c->err);
+    else k_moments<3><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->mpart, c->ticket, c->mom, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st) {
+    k_cardano<<<gs_blocks(n, 256), 256, 0, st>>>(x, y, n, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ou_implicit(ssm_ctx *c) {
+    const double inv = 1.0 - c->h * c->opt.coef_params[0];
+    if (c->d == 1) k_ou_implicit<1><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
+    else if (c->d == 2) k_ou_implicit<2><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
+    else k_ou_implicit<3><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_newton_begin(ssm_ctx *c) {
+    k_newton_begin<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist, c->N, c->Np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32) {
+    k_newton_update<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, c->cnt + pass + 1,
+                                                        c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32,
+                                                        pass, c->kmax, c->passes, c->hist, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_stats(ssm_ctx *c) {
+    k_step_stats<<<1, 1, 0, c->st>>>(c->cnt, c->kmax, c->N, c->counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler(ssm_ctx *c, double bscale) {
+    const int fine_r = c->opt.fine_log2 > 0 ? (int)llround(c->h / (c->T / (double)(1ll << c->opt.fine_log2))) : 1;
+    const double sqrt_hf = c->opt.fine_log2 > 0 ? sqrt(c->T / (double)(1ll << c->opt.fine_log2)) : 0.0;
+    const int chunks = c->plan_drift.chunks;
+    const double lam = c->opt.coef_params[1], eta = c->opt.coef_params[2];
+#define SSM_EUL(D) k_euler<D><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, c->coef, lam, eta, \
+        c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, c->mom, c->err, c->counters)
+    if (c->d == 1) SSM_EUL(1);
+    else if (c->d == 2) SSM_EUL(2);
+    else SSM_EUL(3);
+#undef SSM_EUL
+    k_advance<<<1, 1, 0, c->st>>>(c->dstep, c->counters, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(ssm_ctx *c, long long n) {
+    k_set_step<<<1, 1, 0, c->st>>>(c->dstep, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(const double *a, double *s, int d, int64_t N, int64_t Np, cudaStream_t st) {
+    k_aos_to_soa<<<gs_blocks(N * d, 256), 256, 0, st>>>(a, s, d, N, Np);
+    return cudaGetLastError();
+}
+cudaError_t launch_soa_to_aos(const double *s, double *a, int d, int64_t N, int64_t Np, cudaStream_t st) {
+    k_soa_to_aos<<<gs_blocks(N * d, 256), 256, 0, st>>>(s, a, d, N, Np);
+    return cudaGetLastError();
+}
+cudaError_t launch_stage_b(ssm_ctx *c, double bscale) {
+    k_stage_b<<<gs_blocks(c->N * c->d, 256), 256, 0, c->st>>>(c->part, c->plan_drift.chunks, bscale, c->coef,
+                                                             c->opt.coef_params[1], c->ymean, c->stage, c->d, c->N, c->Np);
+    return cudaGetLastError();
+}
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out, cudaStream_t st) {
+    k_philox<<<gs_blocks(n, 256), 256, 0, st>>>(seed, ctr, n, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_normals(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, double *out, cudaStream_t st) {
+    if (d == 1) k_normals<1><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    else if (d == 2) k_normals<2><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    else k_normals<3><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ssm
