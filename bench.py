@@ -43,7 +43,30 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 comparison (0 = skip)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
+                   help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
+                        "pair pass (13 + 2 launches of k_pair), and exit")
+    p.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"], help="form for --profile-kernels")
+    p.add_argument("--packed", type=int, default=0, help="--profile-kernels: use the packed-FP32 kernels")
     return p.parse_args()
+
+
+def profile_kernels(args):
+    """Small, self-terminating case for ncu: the pair kernels of one step plus one
+    isolated pass of each kind (nothing is timed or printed as a result)."""
+    from paper_2105_09688_gb300 import build as B
+    B.build()
+    import paper_2105_09688_gb300 as S
+    prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
+    s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec)
+    if args.packed:
+        s.set_plan(0, 1, 128, 4)
+        s.set_plan(1, 1, 128, 4)
+    s.step()
+    s.pair_pass(0)
+    s.pair_pass(1)
+    s.sync()
+    s.close()
 
 
 def dist_setup():
@@ -162,6 +185,9 @@ def time_kernel(torch, S, s, stream, which, reps):
 def main():
     args = parse()
     world, rank, local = dist_setup()
+    if args.profile_kernels:
+        profile_kernels(args)
+        return
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -187,6 +213,10 @@ def main():
     s = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream, precision=prec)
     if prec == S.SSM_FP32C_LEARNED:
         S.load_ws(s)
+    s.run_steps(1)
+    tuned_ms = s.autotune()                    # launch shapes, tuned outside the timed region
+    plans = {"step1_pairs": s.plan(0), "drift_pairs": s.plan(1),
+             "tuned_pass_ms": [float(v) for v in tuned_ms]}
     for _ in range(args.warmup):
         s.run_steps(1)
     s.sync()
@@ -229,7 +259,9 @@ def main():
     peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / t_dom / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pair<%s, float>" % ("PK_NEWTON3" if dom == 0 else "PK_DRIFT3"),
+                "traffic": None,
+                "kernel": "%s<%s>" % ("k_pair2" if plans["step1_pairs" if dom == 0 else "drift_pairs"]["packed"]
+                                      else "k_pair", "PK_NEWTON3" if dom == 0 else "PK_DRIFT3"),
                 "peak_basis": "FP32 CUDA-core: 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe max clock)",
                 "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3}
 
@@ -277,7 +309,8 @@ def main():
             "config": {"workload": "coupled3d N=2^18 d=3 h=2^-8 T=1 seed=2", "form": form,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (512 MB write, untimed)",
-                       "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows},
+                       "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows,
+                       "plans": plans},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
             "plain_fp64": fp64,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}

@@ -187,6 +187,24 @@ ssm_status ssm_cardano(const double *x, int64_t n, double h, double *y);
  * *pairs receives the number of pair evaluations enqueued (may be NULL). */
 ssm_status ssm_pair_pass(ssm_ctx *ctx, int which, int64_t *pairs);
 
+/* Autotuner of the pair-sum launch shapes (no counterpart in the paper, whose
+ * runs are on 4 CPU cores): times every compiled shape (scalar or packed-FP32
+ * kernel, threads per block, targets per thread; source chunks chosen to fill
+ * whole waves of the device's resident-block slots) of each pair kind the
+ * context uses, on its current state and stream, and keeps the fastest for
+ * later steps.  best_ms (may be NULL) receives the best per-pass times
+ * [step-1 sums, drift].  Synchronising; overwrites only the partial-sum scratch. */
+ssm_status ssm_autotune(ssm_ctx *ctx, double *best_ms);
+
+/* The launch shape in use for which = 0 (step-1 sums) or 1 (drift):
+ * out[5] = {packed (0/1), threads per block, targets per thread, chunks, sources per chunk}. */
+ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
+
+/* Select a launch shape explicitly: in[3] = {packed (0/1), threads per block,
+ * targets per thread}; the chunk count is planned as in ssm_autotune.
+ * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
+ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
+
 #ifdef __cplusplus
 }
 #endif

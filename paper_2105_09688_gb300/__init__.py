@@ -22,7 +22,8 @@ __all__ = [
     "SSM_FP32C_LEARNED", "SSM_STAGE_Y", "SSM_STAGE_B", "SSMError", "ssm_opts", "ssm_stats_t", "lib",
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
-    "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "SSM",
+    "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
+    "ssm_set_plan", "SSM",
 ]
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
@@ -76,6 +77,9 @@ _SIGS = {
     "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
     "ssm_cardano": (_i32, [_DP, _i64, _dbl, _DP]),
     "ssm_pair_pass": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
+    "ssm_autotune": (_i32, [_vp, _DP]),
+    "ssm_get_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "ssm_set_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
 }
 
 
@@ -205,6 +209,24 @@ def ssm_pair_pass(ctx, which):
     return int(pairs.value)
 
 
+def ssm_autotune(ctx):
+    """Tune the pair-sum launch shapes on the context's state; returns the best pass times (ms)."""
+    best = np.zeros(2)
+    _check(lib().ssm_autotune(ctx, _dp(best)), "ssm_autotune")
+    return best
+
+
+def ssm_get_plan(ctx, which):
+    out = (_i32 * 5)()
+    _check(lib().ssm_get_plan(ctx, int(which), out), "ssm_get_plan")
+    return dict(zip(("packed", "threads", "targets_per_thread", "chunks", "chunk_len"), list(out)))
+
+
+def ssm_set_plan(ctx, which, packed, threads, targets_per_thread):
+    arr = (_i32 * 3)(int(bool(packed)), int(threads), int(targets_per_thread))
+    _check(lib().ssm_set_plan(ctx, int(which), arr), "ssm_set_plan")
+
+
 def ssm_cardano(x, h):
     x = np.ascontiguousarray(x, dtype=np.float64).ravel()
     y = np.empty_like(x)
@@ -267,6 +289,15 @@ class SSM:
 
     def pair_pass(self, which):
         return ssm_pair_pass(self.ctx, which)
+
+    def autotune(self):
+        return ssm_autotune(self.ctx)
+
+    def plan(self, which):
+        return ssm_get_plan(self.ctx, which)
+
+    def set_plan(self, which, packed, threads, targets_per_thread):
+        ssm_set_plan(self.ctx, which, packed, threads, targets_per_thread)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -16,6 +16,8 @@ namespace ssm {
 cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
                       const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st);
 bool pair_shape_supported(int threads, int rpt);
+int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt);
+int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out);
 cudaError_t launch_init_x0(ssm_ctx *c);
 cudaError_t launch_moments(ssm_ctx *c);
 cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st);
@@ -50,24 +52,73 @@ void drift_scale(int coef, bool fp32, int64_t N, double *scale, double *bscale) 
     *bscale = cb / ((double)N * *scale);
 }
 
-// Launch shape of a pair kind: threads x targets-per-thread tiles over the
-// targets, the sources split into chunks so that the grid fills the GPU with
-// several waves of blocks.
-Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
+int64_t padded(int64_t N) { return (N + 127) / 128 * 128; }
+
+// Most source chunks a pass may use: the partial-sum scratch holds
+// chunks * NC * Np doubles, kept under 1 GiB and at most 32 chunks.
+int chunks_cap(int64_t N, int nc) {
+    int64_t cap = (N + SUB - 1) / SUB;
+    if (cap > 32) cap = 32;
+    const int64_t mem = ((int64_t)1 << 30) / ((int64_t)nc * padded(N) * 8);
+    if (cap > mem) cap = mem;
+    return cap < 1 ? 1 : (int)cap;
+}
+
+int kind_nc(int kind) { return kind == PK_NEWTON3 ? 4 : (kind == PK_DRIFT3 ? 3 : 1); }
+
+// Resident-block slots of the device for a pair kernel shape (0 = no device).
+int device_slots(int kind, bool fp32, bool vec2, int threads, int rpt) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    const int nb = pair_blocks_per_sm(kind, fp32, vec2, threads, rpt);
+    if (nb <= 0) { cudaGetLastError(); return 0; }
+    return sms * nb;
+}
+
+// Launch shape of a pair kind: (threads x targets-per-thread) tiles over the
+// targets times source chunks.  All work items cost the same, so the chunk count
+// is chosen to make the number of items fill whole waves of the device's
+// resident-block slots (smallest count reaching 97% wave efficiency with at least
+// two waves, else the most efficient).
+Plan make_plan_shape(int64_t N, int kind, int vec2, int threads, int rpt, int force_chunks, int slots) {
     Plan p;
-    p.threads = 128;
-    p.rpt = fp32 ? (kind == PK_DRIFT1 ? 8 : 4) : 2;
+    p.vec2 = vec2;
+    p.threads = threads;
+    p.rpt = rpt;
     const int64_t tiles = (N + p.threads * p.rpt - 1) / (p.threads * p.rpt);
-    const int64_t max_chunks = (N + SUB - 1) / SUB;
-    int64_t chunks = force_chunks > 0 ? force_chunks : (2432 + tiles - 1) / tiles;   // ~16 blocks per SM
+    const int cap = chunks_cap(N, kind_nc(kind));
+    int64_t chunks;
+    if (force_chunks > 0) {
+        chunks = force_chunks < cap ? force_chunks : cap;
+    } else if (slots > 0) {
+        int64_t best = 1;
+        double best_eff = -1.0;
+        for (int64_t c = 1; c <= cap; ++c) {
+            const int64_t items = tiles * c;
+            const int64_t waves = (items + slots - 1) / slots;
+            const double eff = (double)items / (double)(waves * slots);
+            if (eff >= 0.97 && items >= 2 * (int64_t)slots) { best = c; break; }
+            if (eff > best_eff + 1e-9) { best_eff = eff; best = c; }
+        }
+        chunks = best;
+    } else {
+        chunks = (2432 + tiles - 1) / tiles;
+        if (chunks > cap) chunks = cap;
+    }
     if (chunks < 1) chunks = 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks > 65535) chunks = 65535;
     int64_t len = (N + chunks - 1) / chunks;
     len = (len + SUB - 1) / SUB * SUB;
     p.chunk_len = len;
     p.chunks = (int)((N + len - 1) / len);
     return p;
+}
+
+// Default shape before any tuning: scalar kernels, 128 threads, 4 (FP32 d=3),
+// 8 (FP32 d=1) or 2 (FP64) targets per thread; chunks from the device's slots.
+Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
+    const int th = 128, r = fp32 ? (kind == PK_DRIFT1 ? 8 : 4) : 2;
+    return make_plan_shape(N, kind, 0, th, r, force_chunks, device_slots(kind, fp32, false, th, r));
 }
 
 struct Layout {
@@ -76,9 +127,9 @@ struct Layout {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int64_t padded(int64_t N) { return (N + 127) / 128 * 128; }
-
-Layout make_layout(int d, int64_t N, int coef, const Plan &pn, const Plan &pd, int kmax) {
+// The partial-sum scratch is sized for the largest chunk count the planner may
+// choose, so the layout is known without a device.
+Layout make_layout(int d, int64_t N, int coef, int kmax) {
     Layout L;
     const int64_t Np = padded(N);
     size_t o = 0;
@@ -88,10 +139,10 @@ Layout make_layout(int d, int64_t N, int coef, const Plan &pn, const Plan &pd, i
     L.stage = take(sizeof(double) * d * Np);
     size_t part = 0;
     if (coef == SSM_COEF_COUPLED3D) {
-        part = (size_t)pn.chunks * 4;
-        if ((size_t)pd.chunks * 3 > part) part = (size_t)pd.chunks * 3;
+        part = (size_t)chunks_cap(N, 4) * 4;
+        if ((size_t)chunks_cap(N, 3) * 3 > part) part = (size_t)chunks_cap(N, 3) * 3;
     } else if (coef == SSM_COEF_CUBIC1D_GAUSS) {
-        part = (size_t)pd.chunks;
+        part = (size_t)chunks_cap(N, 1);
     }
     L.part = take(sizeof(double) * part * Np);
     L.mpart = take(sizeof(double) * RED_BLOCKS * 12);
@@ -226,10 +277,7 @@ size_t ssm_workspace_bytes(int d, int64_t N, int coef, const ssm_opts *opts) {
     ssm_opts o;
     if (opts) o = *opts; else fill_defaults(&o);
     if (N < 1 || N > N_MAX || d < 1 || d > 3) return 0;
-    const bool f32 = o.precision != SSM_FP64;
-    Plan pn = make_plan(N, f32, PK_NEWTON3, o.tile_chunks);
-    Plan pd = make_plan(N, f32, coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, o.tile_chunks);
-    return make_layout(d, N, coef, pn, pd, o.newton_kmax).total;
+    return make_layout(d, N, coef, o.newton_kmax).total;
 }
 
 ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t seed, const ssm_opts *opts,
@@ -254,7 +302,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     const bool f32 = o.precision != SSM_FP64;
     c->plan_newton = make_plan(N, f32, PK_NEWTON3, o.tile_chunks);
     c->plan_drift = make_plan(N, f32, coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, o.tile_chunks);
-    Layout L = make_layout(d, N, coef, c->plan_newton, c->plan_drift, c->kmax);
+    Layout L = make_layout(d, N, coef, c->kmax);
 
     cudaError_t e = cudaSuccess;
     if (o.stream) {
@@ -489,6 +537,78 @@ ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
     }
     if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
     if (pairs) *pairs = c->N * c->N;
+    return SSM_OK;
+}
+
+// Time every compiled launch shape of each pair kind this context uses on its
+// current state (CUDA events on the context's stream) and keep the fastest.
+ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
+    if (!c) return SSM_EINVAL;
+    if (c->status != SSM_OK) return (ssm_status)c->status;
+    if (c->coef == SSM_COEF_OU) return SSM_OK;
+    const bool f32 = fp32_pairs(c);
+    double scale, bscale;
+    drift_scale(c->coef, f32, c->N, &scale, &bscale);
+    const int kd = c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3;
+    const int kinds[2] = { PK_NEWTON3, kd };
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SSM_ECUDA;
+    cudaError_t err = cudaSuccess;
+    for (int q = 0; q < 2 && err == cudaSuccess; ++q) {
+        const int kind = kinds[q];
+        if (kind == PK_NEWTON3 && c->coef != SSM_COEF_COUPLED3D) continue;
+        const double *src = kind == PK_NEWTON3 ? c->x : c->y;
+        const double sc = kind == PK_NEWTON3 ? 1.0 : scale;
+        int cand[32][3];
+        const int nc = pair_shape_candidates(kind, f32, cand, 32);
+        Plan best = kind == PK_NEWTON3 ? c->plan_newton : c->plan_drift;
+        float best_t = 1e30f;
+        for (int k = 0; k < nc && err == cudaSuccess; ++k) {
+            const int slots = device_slots(kind, f32, cand[k][0] != 0, cand[k][1], cand[k][2]);
+            if (slots <= 0) continue;
+            Plan p = make_plan_shape(c->N, kind, cand[k][0], cand[k][1], cand[k][2], c->opt.tile_chunks, slots);
+            err = pair_sums(kind, f32, p, src, c->y, nullptr, nullptr, c->N, c->Np, sc, c->part, c->st);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->st);
+            for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)
+                err = pair_sums(kind, f32, p, src, c->y, nullptr, nullptr, c->N, c->Np, sc, c->part, c->st);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c->st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms < best_t) { best_t = ms; best = p; }
+        }
+        if (kind == PK_NEWTON3) c->plan_newton = best; else c->plan_drift = best;
+        if (best_ms) best_ms[q] = best_t / 2.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) { c->status = cuda_status(err); return (ssm_status)c->status; }
+    if (c->graph_ready) { cudaGraphExecDestroy(c->gexec); c->graph_ready = false; }
+    return SSM_OK;
+}
+
+ssm_status ssm_get_plan(ssm_ctx *c, int which, int *out) {
+    if (!c || !out || (which != 0 && which != 1)) return SSM_EINVAL;
+    const Plan &p = which == 0 ? c->plan_newton : c->plan_drift;
+    out[0] = p.vec2; out[1] = p.threads; out[2] = p.rpt; out[3] = p.chunks; out[4] = (int)p.chunk_len;
+    return SSM_OK;
+}
+
+ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
+    if (!c || !in || (which != 0 && which != 1)) return SSM_EINVAL;
+    if (c->coef == SSM_COEF_OU || (which == 0 && c->coef != SSM_COEF_COUPLED3D)) return SSM_EINVAL;
+    const bool f32 = fp32_pairs(c);
+    const int kind = which == 0 ? PK_NEWTON3 : (c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3);
+    int cand[32][3];
+    const int nc = pair_shape_candidates(kind, f32, cand, 32);
+    bool ok = false;
+    for (int k = 0; k < nc; ++k)
+        if (cand[k][0] == (in[0] != 0) && cand[k][1] == in[1] && cand[k][2] == in[2]) ok = true;
+    if (!ok) return SSM_EINVAL;
+    const int slots = device_slots(kind, f32, in[0] != 0, in[1], in[2]);
+    Plan p = make_plan_shape(c->N, kind, in[0] != 0, in[1], in[2], c->opt.tile_chunks, slots);
+    if (which == 0) c->plan_newton = p; else c->plan_drift = p;
+    if (c->graph_ready) { cudaGraphExecDestroy(c->gexec); c->graph_ready = false; }
     return SSM_OK;
 }
 

@@ -173,8 +173,134 @@ k_pair(const double *__restrict__ src, const double *__restrict__ tgt, const int
 }
 
 // ---------------------------------------------------------------------------
-// Host launchers.  Launch shapes (threads, targets per thread) are compiled-in
-// candidates; the chunk count comes from the plan.
+// Packed-FP32 form (sm_100+ FFMA2/FADD2/FMUL2: two FP32 lanes per instruction).
+// Targets are held in pairs: target 2k in .x and 2k+1 in .y of a float2, and a
+// source coordinate is broadcast to both halves (stored duplicated in shared
+// memory), so one packed instruction advances two pair interactions.  Same
+// arithmetic as the scalar FP32 form, term for term.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int KIND>
+__device__ __forceinline__ void pair2(float2 sx, float2 sy, float2 sz, float2 ntx, float2 nty, float2 ntz,
+                                      float2 *acc);
+template <> __device__ __forceinline__ void pair2<PK_NEWTON3>(float2 sx, float2 sy, float2 sz, float2 ntx,
+                                                              float2 nty, float2 ntz, float2 *acc) {
+    const float2 dx = __fadd2_rn(sx, ntx), dy = __fadd2_rn(sy, nty), dz = __fadd2_rn(sz, ntz);
+    float2 q = __ffma2_rn(dx, dx, f2(1.0f, 1.0f));
+    q = __ffma2_rn(dy, dy, q);
+    q = __ffma2_rn(dz, dz, q);
+    const float2 w = f2(rcp_approx(q.x), rcp_approx(q.y));
+    acc[0] = __ffma2_rn(w, dx, acc[0]);
+    acc[1] = __ffma2_rn(w, dy, acc[1]);
+    acc[2] = __ffma2_rn(w, dz, acc[2]);
+    acc[3] = __fadd2_rn(acc[3], w);
+}
+template <> __device__ __forceinline__ void pair2<PK_DRIFT3>(float2 sx, float2 sy, float2 sz, float2 ntx,
+                                                             float2 nty, float2 ntz, float2 *acc) {
+    const float2 dx = __fadd2_rn(sx, ntx), dy = __fadd2_rn(sy, nty), dz = __fadd2_rn(sz, ntz);
+    const float2 mdz = f2(-dz.x, -dz.y), mdy = f2(-dy.x, -dy.y), mdx = f2(-dx.x, -dx.y);
+    const float2 nq = __ffma2_rn(mdx, dx, __ffma2_rn(mdy, dy, __fmul2_rn(mdz, dz)));
+    const float2 e = f2(ex2_approx(nq.x), ex2_approx(nq.y));
+    acc[0] = __ffma2_rn(e, dx, acc[0]);
+    acc[1] = __ffma2_rn(e, dy, acc[1]);
+    acc[2] = __ffma2_rn(e, dz, acc[2]);
+}
+
+template <int KIND, int THREADS, int R>
+__global__ void __launch_bounds__(THREADS)
+k_pair2(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
+        const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
+        double *__restrict__ part) {
+    static_assert(R % 2 == 0, "targets per thread come in pairs");
+    constexpr int NC = KindInfo<KIND>::NC, R2 = R / 2;
+    __shared__ float4 sxy[SUB];   // (x, x, y, y)
+    __shared__ float2 szz[SUB];   // (z, z)
+
+    const int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
+    if (t0 >= ntgt) return;
+    const int tid = threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t j0 = (int64_t)chunk * chunk_len;
+    const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
+
+    float2 ntx[R2], nty[R2], ntz[R2];
+#pragma unroll
+    for (int k = 0; k < R2; ++k) {
+        float v[2][3];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t t = t0 + (2 * k + e) * THREADS + tid;
+            int64_t i = 0;
+            if (t < ntgt) i = act ? (int64_t)act[t] : t;
+            v[e][0] = -(float)(tgt[i] * scale);
+            v[e][1] = -(float)(tgt[Np + i] * scale);
+            v[e][2] = -(float)(tgt[2 * Np + i] * scale);
+        }
+        ntx[k] = f2(v[0][0], v[1][0]);
+        nty[k] = f2(v[0][1], v[1][1]);
+        ntz[k] = f2(v[0][2], v[1][2]);
+    }
+    float2 acc[R2][NC], hi[R2][NC], lo[R2][NC];
+#pragma unroll
+    for (int k = 0; k < R2; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[k][c] = f2(0.f, 0.f); hi[k][c] = f2(0.f, 0.f); lo[k][c] = f2(0.f, 0.f); }
+
+    for (int64_t base = j0; base < j1; base += SUB) {
+        const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
+        __syncthreads();
+        for (int s = tid; s < ns; s += THREADS) {
+            const int64_t j = base + s;
+            const float x = (float)(src[j] * scale), y = (float)(src[Np + j] * scale), z = (float)(src[2 * Np + j] * scale);
+            sxy[s] = make_float4(x, x, y, y);
+            szz[s] = f2(z, z);
+        }
+        __syncthreads();
+        if (ns == SUB) {
+#pragma unroll 4
+            for (int s = 0; s < SUB; ++s) {
+                const float4 a = sxy[s];
+                const float2 b = szz[s];
+#pragma unroll
+                for (int k = 0; k < R2; ++k) pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], acc[k]);
+            }
+        } else {
+            for (int s = 0; s < ns; ++s) {
+                const float4 a = sxy[s];
+                const float2 b = szz[s];
+#pragma unroll
+                for (int k = 0; k < R2; ++k) pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R2; ++k)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                two_sum_acc(hi[k][c].x, lo[k][c].x, acc[k][c].x);
+                two_sum_acc(hi[k][c].y, lo[k][c].y, acc[k][c].y);
+                acc[k][c] = f2(0.f, 0.f);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < R2; ++k)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t t = t0 + (2 * k + e) * THREADS + tid;
+            if (t < ntgt) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const double v = e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
+                    part[((int64_t)chunk * NC + c) * Np + t] = v;
+                }
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.  Launch shapes (threads, targets per thread, packed or
+// scalar FP32) are compiled-in candidates; the chunk count comes from the plan.
 // ---------------------------------------------------------------------------
 template <int KIND, typename T, int THREADS, int R>
 static cudaError_t launch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
@@ -184,9 +310,19 @@ static cudaError_t launch(const Plan &p, const double *src, const double *tgt, c
     k_pair<KIND, T, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
     return cudaGetLastError();
 }
+template <int KIND, int THREADS, int R>
+static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
+                           int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+    const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
+    dim3 grid((unsigned)tiles, (unsigned)p.chunks);
+    k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+    return cudaGetLastError();
+}
 
-// The (threads, rpt) shapes each kind is compiled for.
+// The (threads, targets per thread) shapes compiled for the scalar and the
+// packed kernels.
 #define SSM_PAIR_SHAPES(X) X(128, 2) X(128, 4) X(256, 2) X(256, 4) X(128, 8)
+#define SSM_PAIR2_SHAPES(X) X(128, 4) X(128, 8) X(256, 4) X(256, 8)
 
 template <int KIND, typename T>
 static cudaError_t dispatch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
@@ -197,9 +333,23 @@ static cudaError_t dispatch(const Plan &p, const double *src, const double *tgt,
 #undef SSM_CASE
     return cudaErrorInvalidValue;
 }
+template <int KIND>
+static cudaError_t dispatch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
+                             int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+#define SSM_CASE(TH, RR) \
+    if (p.threads == TH && p.rpt == RR) return launch2<KIND, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+    SSM_PAIR2_SHAPES(SSM_CASE)
+#undef SSM_CASE
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
                       const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+    if (fp32 && p.vec2) {
+        if (kind == PK_NEWTON3) return dispatch2<PK_NEWTON3>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+        if (kind == PK_DRIFT3) return dispatch2<PK_DRIFT3>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+        return cudaErrorInvalidValue;
+    }
     switch (kind) {
     case PK_DRIFT1:
         return fp32 ? dispatch<PK_DRIFT1, float>(p, src, tgt, act, cnt, N, Np, scale, part, st)
@@ -214,11 +364,57 @@ cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, con
     return cudaErrorInvalidValue;
 }
 
-bool pair_shape_supported(int threads, int rpt) {
-#define SSM_CASE(TH, RR) if (threads == TH && rpt == RR) return true;
+template <int KIND, typename T>
+static int occ_dispatch(int threads, int rpt) {
+    int nb = 0;
+#define SSM_CASE(TH, RR) \
+    if (threads == TH && rpt == RR) { \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<KIND, T, TH, RR>, TH, 0) != cudaSuccess) nb = 0; \
+        return nb; }
     SSM_PAIR_SHAPES(SSM_CASE)
 #undef SSM_CASE
-    return false;
+    return 0;
+}
+template <int KIND>
+static int occ_dispatch2(int threads, int rpt) {
+    int nb = 0;
+#define SSM_CASE(TH, RR) \
+    if (threads == TH && rpt == RR) { \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair2<KIND, TH, RR>, TH, 0) != cudaSuccess) nb = 0; \
+        return nb; }
+    SSM_PAIR2_SHAPES(SSM_CASE)
+#undef SSM_CASE
+    return 0;
+}
+
+// Resident blocks per SM of a pair kernel shape (0 if unknown / no device).
+int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt) {
+    if (fp32 && vec2) {
+        if (kind == PK_NEWTON3) return occ_dispatch2<PK_NEWTON3>(threads, rpt);
+        if (kind == PK_DRIFT3) return occ_dispatch2<PK_DRIFT3>(threads, rpt);
+        return 0;
+    }
+    switch (kind) {
+    case PK_DRIFT1: return fp32 ? occ_dispatch<PK_DRIFT1, float>(threads, rpt) : occ_dispatch<PK_DRIFT1, double>(threads, rpt);
+    case PK_DRIFT3: return fp32 ? occ_dispatch<PK_DRIFT3, float>(threads, rpt) : occ_dispatch<PK_DRIFT3, double>(threads, rpt);
+    case PK_NEWTON3: return fp32 ? occ_dispatch<PK_NEWTON3, float>(threads, rpt) : occ_dispatch<PK_NEWTON3, double>(threads, rpt);
+    }
+    return 0;
+}
+
+// Candidate launch shapes of a pair kind for the autotuner: {vec2, threads, rpt}.
+int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out) {
+    int n = 0;
+    auto add = [&](int v, int th, int r) { if (n < max_out) { out[n][0] = v; out[n][1] = th; out[n][2] = r; ++n; } };
+#define SSM_CASE(TH, RR) add(0, TH, RR);
+    SSM_PAIR_SHAPES(SSM_CASE)
+#undef SSM_CASE
+    if (fp32 && (kind == PK_NEWTON3 || kind == PK_DRIFT3)) {
+#define SSM_CASE(TH, RR) add(1, TH, RR);
+        SSM_PAIR2_SHAPES(SSM_CASE)
+#undef SSM_CASE
+    }
+    return n;
 }
 
 }  // namespace ssm

@@ -204,6 +204,46 @@ def test_coupled3d_fp32c_full_horizon_tolerances(S):
     assert np.max(np.abs(var_g - var_o)) < 1e-5
 
 
+@pytest.mark.parametrize("shape", [(1, 128, 4), (1, 256, 8), (1, 128, 8), (0, 256, 2), (0, 128, 8)])
+def test_coupled3d_fp32c_every_launch_shape(S, shape):
+    """Packed and scalar FP32 pair kernels of each compiled shape give the oracle's
+    result within FP32-compensated accuracy (N = 1000: ragged tiles and chunks)."""
+    N, h, K = 1000, 2.0 ** -8, 8
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=11, precision=S.SSM_FP32C)
+    s.set_plan(0, *shape)
+    s.set_plan(1, *shape)
+    assert s.plan(0)["packed"] == shape[0] and s.plan(0)["targets_per_thread"] == shape[2]
+    s.run_steps(K)
+    x, _ = s.get_state()
+    s.close()
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=11)
+    xo = O.run(P, O.init_x0(P), 0, K)
+    assert np.max(np.abs(x - xo)) < 1e-7
+
+
+def test_autotune_changes_shape_not_results(S):
+    N, h = 5000, 2.0 ** -8
+    runs = []
+    for tune in (False, True):
+        s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=12, precision=S.SSM_FP32C)
+        if tune:
+            best = s.autotune()
+            assert np.all(best > 0)
+        s.run_steps(3)
+        runs.append(s.get_state()[0])
+        s.close()
+    assert np.max(np.abs(runs[0] - runs[1])) < 1e-8
+
+
+def test_set_plan_rejects_unknown_shape(S):
+    s = S.SSM(d=3, N=100, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=1)   # FP64: no packed kernels
+    with pytest.raises(S.SSMError):
+        s.set_plan(0, 1, 128, 4)
+    with pytest.raises(S.SSMError):
+        s.set_plan(0, 0, 96, 4)
+    s.close()
+
+
 def test_coupled3d_full_size_sampled_fp32c(S):
     """N = 2^18, h = 2^-8, seed 2 (the benchmark workload): one step, sampled."""
     N, h = 1 << 18, 2.0 ** -8
