@@ -205,6 +205,31 @@ ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
 
+/* Step-2 pair drift without any allocation (the paper has no counterpart; this
+ * is a convenience for callers that cannot allocate device memory when they need
+ * it -- code in host callbacks or real-time loops that must not block on the
+ * allocator, or runtimes that hand out one pre-reserved memory pool).
+ *
+ * Computes, for coef = SSM_COEF_CUBIC1D_GAUSS (d = 1) or SSM_COEF_COUPLED3D
+ * (d = 3) and precision SSM_FP64 or SSM_FP32C, the drift b(y_i, mu^y) of that
+ * coefficient set for the N particles y (device array, SoA: component c of
+ * particle i at y[c*ld + i], ld >= N) into b (device array, same layout), on
+ * `stream` (cudaStream_t, NULL = default stream).  Asynchronous.  The result is
+ * the one ssm_get_stage(SSM_STAGE_B) reports after a step whose Y is y.
+ *
+ * Its scratch is a fixed 8 MiB static device array inside the library (held by
+ * every GPU that loads the library until the process exits), so d * ld must be
+ * at most 2^20 (ld <= 349,525 for d = 3, <= 1,048,576 for d = 1); larger sizes
+ * return SSM_ENOMEM and launch nothing.  The call allocates and frees nothing.
+ * The first call on a device looks up the scratch array's device address on
+ * that device (it must be current); make that first call before any stream
+ * capture.  All calls share the scratch: calls that overlap on the GPU (other
+ * streams, unordered threads) race; calls on one stream are safe.  Nothing in
+ * the scratch needs to start at zero.  SSM_EINVAL for null pointers, N < 1,
+ * ld < N or an unsupported coef/precision. */
+ssm_status ssm_drift_noalloc(int coef, int precision, int64_t N, const double *y, int64_t ld, double *b,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "SSM",
+    "ssm_set_plan", "ssm_drift_noalloc", "SSM",
 ]
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
@@ -80,6 +80,7 @@ _SIGS = {
     "ssm_autotune": (_i32, [_vp, _DP]),
     "ssm_get_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ssm_set_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "ssm_drift_noalloc": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _vp]),
 }
 
 
@@ -225,6 +226,14 @@ def ssm_get_plan(ctx, which):
 def ssm_set_plan(ctx, which, packed, threads, targets_per_thread):
     arr = (_i32 * 3)(int(bool(packed)), int(threads), int(targets_per_thread))
     _check(lib().ssm_set_plan(ctx, int(which), arr), "ssm_set_plan")
+
+
+def ssm_drift_noalloc(coef, precision, N, y_ptr, ld, b_ptr, stream_ptr=0):
+    """Step-2 drift of the device arrays at y_ptr into b_ptr (SoA, leading dimension ld)
+    without allocating (scratch is a fixed static device array; see include/ssm.h).
+    For callers that cannot allocate device memory at the point of use."""
+    _check(lib().ssm_drift_noalloc(int(coef), int(precision), int(N), _vp(int(y_ptr)), int(ld), _vp(int(b_ptr)),
+                                   _vp(int(stream_ptr)) if stream_ptr else None), "ssm_drift_noalloc")
 
 
 def ssm_cardano(x, h):
