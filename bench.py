@@ -282,6 +282,33 @@ def main():
            "steps": e2e_steps}
     s.close()
 
+    # the same FP32C form without the learned start (same launch shapes, same timing)
+    fp32c_plain = None
+    if form.startswith("learned"):
+        q = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+                  precision=S.SSM_FP32C)
+        for w in (0, 1):
+            pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
+            q.set_plan(w, pl["packed"], pl["threads"], pl["targets_per_thread"])
+        for _ in range(args.warmup):
+            q.run_steps(1)
+        q.sync()
+        qs0 = q.stats()
+        qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            qev[k][0].record(stream)
+            q.run_steps(1)
+            qev[k][1].record(stream)
+        torch.cuda.synchronize()
+        qt = sum(a.elapsed_time(b) / 1e3 for a, b in qev)
+        qs1 = q.stats()
+        fp32c_plain = {"value": N_PART * args.steps / qt, "unit": "particle-steps/s",
+                       "ms_per_step": 1e3 * qt / args.steps,
+                       "newton_rows_per_step": (qs1["newton_rows"] - qs0["newton_rows"]) / args.steps}
+        q.close()
+
     # plain FP64 GPU SSM on the same workload (comparison of the metric)
     fp64 = None
     if args.fp64_steps > 0:
@@ -312,6 +339,8 @@ def main():
                        "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows,
                        "plans": plans},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+            "fp32c_without_learned_start": fp32c_plain,
+            "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
             "plain_fp64": fp64,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

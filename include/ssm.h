@@ -91,7 +91,7 @@ typedef struct {
     size_t workspace_bytes;
     int tile_chunks;        /* 0 = tuned; else number of source chunks per pair pass */
     int ws_passes;          /* learned form: passes from the learned start before the
-                               plain restart; default 3 */
+                               plain restart; default 4 */
 } ssm_opts;
 
 typedef struct {
@@ -204,6 +204,58 @@ ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
  * targets per thread}; the chunk count is planned as in ssm_autotune.
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
+
+/* ---- learned initial guess of step 1 (SSM_FP32C_LEARNED, SSM_COEF_COUPLED3D) ----
+ * The paper has no counterpart; its step 1 (§2.3, eq. SSTM:scheme 1) only needs
+ * some convergent solver.  A network 16 -> 64 -> 64 -> 64 -> 3 (SiLU, BF16
+ * weights, FP32 arithmetic) maps the features f = (x_i (3), the raw moments
+ * m_k = (1/N) sum_j x_j^k, k = 1..4, per coordinate (12, k-major), h) of particle i
+ * to the converged pair sum S(Y*_i) = (1/N) sum_j (X_j - Y*_i)/(1 + |X_j - Y*_i|^2);
+ * step 1 then starts from the root of u = x_i + h(-u|u|^2 + S_pred/2) and runs the
+ * usual passes.  A particle whose residual still exceeds newton_tol after
+ * ssm_opts.ws_passes passes restarts from the plain start Y = X (plain Newton is
+ * the judge); ssm_stats reports those restarts as fallbacks.
+ *
+ * Network parameters travel as one "blob" of ssm_ws_blob_bytes() bytes: header
+ * (magic 0x57534D53, version 1, 16, 64, 3), feature mean/std [16]/[16], label
+ * mean/std [4]/[4], biases b1, b2, b3 [64] and b4 [4] in FP32, then BF16 weights
+ * W1 [64][16], W2 [64][64], W3 [64][64], W4 [4][64] (row-major, row 3 of W4 zero).
+ * All arrays of these functions are host arrays owned by the caller. */
+size_t ssm_ws_blob_bytes(void);
+
+/* Number of trainable parameters (order W1, b1, W2, b2, W3, b3, W4 [3][64], b4). */
+int ssm_ws_num_params(void);
+
+/* Load a blob into a SSM_COEF_COUPLED3D context; with precision
+ * SSM_FP32C_LEARNED the following steps use the learned start. */
+ssm_status ssm_ws_load(ssm_ctx *ctx, const void *blob, size_t bytes);
+
+/* Training rows from the context's last step, for particles i = offset,
+ * offset + stride, ... < N: feat[r*16 + ...] = (X_n,i, moments of X_n, h) and
+ * label[r*3 + c] = S(Y*_n,i); *rows receives the count.  X_n,i is rebuilt as
+ * Y* - h v(Y*), exact up to the residual tolerance.  SSM_ESTATE before any step. */
+ssm_status ssm_ws_collect(ssm_ctx *ctx, int64_t stride, int64_t offset, float *feat, float *label, int64_t *rows);
+
+/* Network outputs (S_pred, unstandardised) for n feature rows: out[n*3]. */
+ssm_status ssm_ws_predict(const void *blob, size_t bytes, const float *feat, int64_t n, float *out);
+
+/* One forward + backward pass over n <= 2^20 rows: grad[num_params] = gradient of
+ * the mean over rows and outputs of (net(f) - (label - mean)/std)^2 w.r.t. the
+ * parameters (weights at their BF16 values); *loss = that mean (may be NULL). */
+ssm_status ssm_ws_grad(const void *blob, size_t bytes, const float *feat, const float *label, int64_t n,
+                       float *grad, double *loss);
+
+/* Train a network on n rows: minibatch Adam (batch <= 65536), `epochs` shuffled
+ * passes, learning rate lr with cosine decay to lr/20, weights initialised
+ * N(0, 1/fan_in) from `seed`, feature and label statistics from the data.  Writes
+ * the blob to blob_out (bytes >= ssm_ws_blob_bytes()) and the mean loss of each
+ * epoch to loss_curve[epochs] (may be NULL).  Synchronous; uses its own device
+ * buffers on the default stream. */
+ssm_status ssm_ws_train(const float *feat, const float *label, int64_t n, int epochs, int batch, float lr,
+                        uint64_t seed, void *blob_out, size_t bytes, double *loss_curve);
+
+/* The parameter vector of a blob (weights at their BF16 values): params[num_params]. */
+ssm_status ssm_ws_params(const void *blob, size_t bytes, float *params);
 
 /* Step-2 pair drift without any allocation (the paper has no counterpart; this
  * is a convenience for callers that cannot allocate device memory when they need

@@ -32,6 +32,14 @@ SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
 SSM_STAGE_Y, SSM_STAGE_B = 0, 1
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libssm.so")
+# Learned-start network trained by train_ws.py (rows from plain-SSM runs, seeds 100..163).
+WS_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "ws_weights.bin")
+
+
+def load_ws(s, path=WS_WEIGHTS):
+    """Load the shipped learned-start network into an SSM context."""
+    with open(path, "rb") as f:
+        s.ws_load(f.read())
 
 _i32, _i64, _u64, _dbl, _sz, _vp = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
                                     ctypes.c_size_t, ctypes.c_void_p)
@@ -81,7 +89,88 @@ _SIGS = {
     "ssm_get_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ssm_set_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ssm_drift_noalloc": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _vp]),
+    "ssm_ws_blob_bytes": (_sz, []),
+    "ssm_ws_num_params": (_i32, []),
+    "ssm_ws_load": (_i32, [_vp, _vp, _sz]),
+    "ssm_ws_collect": (_i32, [_vp, _i64, _i64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                              ctypes.POINTER(_i64)]),
+    "ssm_ws_predict": (_i32, [_vp, _sz, ctypes.POINTER(ctypes.c_float), _i64, ctypes.POINTER(ctypes.c_float)]),
+    "ssm_ws_grad": (_i32, [_vp, _sz, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _i64,
+                           ctypes.POINTER(ctypes.c_float), _DP]),
+    "ssm_ws_train": (_i32, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _i64, _i32, _i32,
+                            ctypes.c_float, _u64, _vp, _sz, _DP]),
+    "ssm_ws_params": (_i32, [_vp, _sz, ctypes.POINTER(ctypes.c_float)]),
 }
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_FP)
+
+
+def _blob_arg(blob):
+    b = np.ascontiguousarray(np.frombuffer(bytes(blob), dtype=np.uint8))
+    return b, b.ctypes.data_as(_vp), b.size
+
+
+def ssm_ws_blob_bytes():
+    return int(lib().ssm_ws_blob_bytes())
+
+
+def ssm_ws_num_params():
+    return int(lib().ssm_ws_num_params())
+
+
+def ssm_ws_load(ctx, blob):
+    keep, p, n = _blob_arg(blob)
+    _check(lib().ssm_ws_load(ctx, p, n), "ssm_ws_load")
+
+
+def ssm_ws_collect(ctx, N, stride, offset):
+    rows = max(0, (N - offset + stride - 1) // stride)
+    feat = np.empty((rows, 16), np.float32)
+    label = np.empty((rows, 3), np.float32)
+    got = _i64(0)
+    _check(lib().ssm_ws_collect(ctx, int(stride), int(offset), _fp(feat), _fp(label), ctypes.byref(got)),
+           "ssm_ws_collect")
+    return feat[:got.value], label[:got.value]
+
+
+def ssm_ws_predict(blob, feat):
+    keep, p, n = _blob_arg(blob)
+    feat = np.ascontiguousarray(feat, np.float32).reshape(-1, 16)
+    out = np.empty((feat.shape[0], 3), np.float32)
+    _check(lib().ssm_ws_predict(p, n, _fp(feat), feat.shape[0], _fp(out)), "ssm_ws_predict")
+    return out
+
+
+def ssm_ws_grad(blob, feat, label):
+    keep, p, n = _blob_arg(blob)
+    feat = np.ascontiguousarray(feat, np.float32).reshape(-1, 16)
+    label = np.ascontiguousarray(label, np.float32).reshape(-1, 3)
+    g = np.empty(ssm_ws_num_params(), np.float32)
+    loss = _dbl(0.0)
+    _check(lib().ssm_ws_grad(p, n, _fp(feat), _fp(label), feat.shape[0], _fp(g), ctypes.byref(loss)), "ssm_ws_grad")
+    return g, float(loss.value)
+
+
+def ssm_ws_train(feat, label, epochs=20, batch=8192, lr=2e-3, seed=0):
+    """Train the learned-start network on the GPU; returns (blob bytes, per-epoch losses)."""
+    feat = np.ascontiguousarray(feat, np.float32).reshape(-1, 16)
+    label = np.ascontiguousarray(label, np.float32).reshape(-1, 3)
+    blob = np.zeros(ssm_ws_blob_bytes(), np.uint8)
+    curve = np.zeros(int(epochs))
+    _check(lib().ssm_ws_train(_fp(feat), _fp(label), feat.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                              blob.ctypes.data_as(_vp), blob.size, _dp(curve)), "ssm_ws_train")
+    return blob.tobytes(), curve
+
+
+def ssm_ws_params(blob):
+    keep, p, n = _blob_arg(blob)
+    out = np.empty(ssm_ws_num_params(), np.float32)
+    _check(lib().ssm_ws_params(p, n, _fp(out)), "ssm_ws_params")
+    return out
 
 
 def lib():
@@ -307,6 +396,12 @@ class SSM:
 
     def set_plan(self, which, packed, threads, targets_per_thread):
         ssm_set_plan(self.ctx, which, packed, threads, targets_per_thread)
+
+    def ws_load(self, blob):
+        ssm_ws_load(self.ctx, blob)
+
+    def ws_collect(self, stride, offset=0):
+        return ssm_ws_collect(self.ctx, self.N, stride, offset)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -122,7 +122,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -159,6 +159,8 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.counters = take(sizeof(long long) * CNT_N);
     L.hist = take(sizeof(long long) * 16);
     L.wsw = take(nt ? 65536 * sizeof(float) : 0);
+    L.sconv = take(nt ? sizeof(double) * 3 * Np : 0);
+    L.mom_prev = take(sizeof(double) * 12);
     L.total = o;
     return L;
 }
@@ -171,7 +173,7 @@ void fill_defaults(ssm_opts *o) {
     o->fine_log2 = 0;
     o->x0_mean = 0.0;
     o->x0_std = 1.0;
-    o->ws_passes = 3;
+    o->ws_passes = 4;
 }
 
 ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_opts &o) {
@@ -287,7 +289,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     ssm_opts o;
     if (opts) o = *opts; else fill_defaults(&o);
     if (o.newton_kmax == 0) o.newton_kmax = 12;
-    if (o.ws_passes <= 0) o.ws_passes = 3;
+    if (o.ws_passes <= 0) o.ws_passes = 4;
     ssm_status s = check_args(d, N, h, T, coef, o);
     if (s != SSM_OK) return s;
 
@@ -340,6 +342,8 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->dstep = (long long *)(b + L.dstep); c->counters = (long long *)(b + L.counters);
     c->hist = (long long *)(b + L.hist);
     c->ws_w = (float *)(b + L.wsw);
+    c->sconv = (double *)(b + L.sconv);
+    c->mom_prev = (double *)(b + L.mom_prev);
     c->ws_loaded = 0;
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0

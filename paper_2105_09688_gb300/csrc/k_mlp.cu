@@ -1,9 +1,637 @@
-// k_mlp.cu -- learned initial guess of the implicit step (filled in with the
-// network kernels).
+// k_mlp.cu -- learned initial guess for step 1 of the coupled workload.
+//
+// A small network predicts, from particle i's state and the moments of the
+// empirical measure, the converged pair sum S(Y*_i) = (1/N) sum_j (X_j - Y*_i) /
+// (1 + |X_j - Y*_i|^2) of step 1 (§2.3, eq. SSTM:scheme 1).  The start Y^0 is then
+// the exact root of the per-particle cubic u = X + h(-u|u|^2 + 0.5 S_pred), so the
+// network only has to learn the smooth measure-dependent part.  The Newton-type
+// passes of k_newton_update run from that start; a particle whose residual still
+// exceeds the tolerance after `ws_passes` passes restarts from the plain start
+// Y = X (plain Newton judges the learned start).  The paper has no counterpart.
+//
+// Network: features f = (x_1, x_2, x_3, m_1..m_4 per coordinate (12), h) = 16,
+// standardised with the training set's mean and standard deviation;
+// 16 -> 64 -> 64 -> 64 -> 3, SiLU on the hidden layers, weights stored in BF16,
+// biases and all arithmetic in FP32.  The whole forward is ~9.4k FMA per
+// particle, ~0.2% of a step at N = 2^18, so it runs on CUDA-core FMAs with the
+// weights broadcast from shared memory.
+//
+// Training (ssm_ws_train) is plain minibatch Adam on the mean squared error of
+// the standardised outputs, with FP32 master weights and the forward run on the
+// BF16-rounded weights; every step runs in the kernels below.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
 
+#include <vector>
+
+#include "ssm.h"
 #include "ssm_device.cuh"
 
 namespace ssm {
-cudaError_t ws_forward_start(ssm_ctx *) { return cudaErrorNotSupported; }
+
+constexpr int NI = 16, NH = 64, NO = 3;
+// Blob layout, in 32-bit words.
+constexpr uint32_t WS_MAGIC = 0x57534D53u, WS_VERSION = 1u;
+constexpr int OFF_FMEAN = 8, OFF_FSTD = 24, OFF_YMEAN = 40, OFF_YSTD = 44;
+constexpr int OFF_B1 = 48, OFF_B2 = 112, OFF_B3 = 176, OFF_B4 = 240;
+constexpr int OFF_W = 244;                               // bf16 weights start here
+constexpr int NW1 = NH * NI, NW2 = NH * NH, NW3 = NH * NH, NW4 = 4 * NH;   // W4 padded to 4 rows
+constexpr int BLOB_WORDS = OFF_W + (NW1 + NW2 + NW3 + NW4) / 2;
+constexpr size_t BLOB_BYTES = (size_t)BLOB_WORDS * 4;
+// Master parameter vector (training): W1, b1, W2, b2, W3, b3, W4 (3 x 64), b4.
+constexpr int P_W1 = 0, P_B1 = P_W1 + NW1, P_W2 = P_B1 + NH, P_B2 = P_W2 + NW2, P_W3 = P_B2 + NH, P_B3 = P_W3 + NW3,
+              P_W4 = P_B3 + NH, P_B4 = P_W4 + NO * NH, NPARAM = P_B4 + NO;
+
+struct Net {                    // FP32 view of the network in shared memory
+    float W1[NW1], W2[NW2], W3[NW3], W4[NO * NH];
+    float b1[NH], b2[NH], b3[NH], b4[4];
+    float fm[NI], fs[NI], ym[4], ys[4];
+};
+
+__device__ __forceinline__ float silu(float s) { return s / (1.0f + __expf(-s)); }
+__device__ __forceinline__ float dsilu(float s) {
+    const float g = 1.0f / (1.0f + __expf(-s));
+    return g * (1.0f + s * (1.0f - g));
+}
+
+// Cooperative load of a blob into shared memory (block-wide).
+__device__ void load_net(const float *__restrict__ blob, Net &n) {
+    const __nv_bfloat16 *w = reinterpret_cast<const __nv_bfloat16 *>(blob + OFF_W);
+    for (int k = threadIdx.x; k < NW1; k += blockDim.x) n.W1[k] = __bfloat162float(w[k]);
+    for (int k = threadIdx.x; k < NW2; k += blockDim.x) n.W2[k] = __bfloat162float(w[NW1 + k]);
+    for (int k = threadIdx.x; k < NW3; k += blockDim.x) n.W3[k] = __bfloat162float(w[NW1 + NW2 + k]);
+    for (int k = threadIdx.x; k < NO * NH; k += blockDim.x) n.W4[k] = __bfloat162float(w[NW1 + NW2 + NW3 + k]);
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+        n.b1[k] = blob[OFF_B1 + k];
+        n.b2[k] = blob[OFF_B2 + k];
+        n.b3[k] = blob[OFF_B3 + k];
+    }
+    if (threadIdx.x < 4) {
+        n.b4[threadIdx.x] = blob[OFF_B4 + threadIdx.x];
+        n.ym[threadIdx.x] = blob[OFF_YMEAN + threadIdx.x];
+        n.ys[threadIdx.x] = blob[OFF_YSTD + threadIdx.x];
+    }
+    if (threadIdx.x < NI) {
+        n.fm[threadIdx.x] = blob[OFF_FMEAN + threadIdx.x];
+        n.fs[threadIdx.x] = blob[OFF_FSTD + threadIdx.x];
+    }
+}
+
+// Per-thread activation column in shared memory, after the Net: element k of
+// thread t at col[k * blockDim.x] (col = base + t), so the outer loops over
+// neurons need not be unrolled (registers hold only the current layer's input).
+__device__ __forceinline__ float *act_column() {
+    extern __shared__ float smem[];
+    return smem + sizeof(Net) / sizeof(float) + threadIdx.x;
+}
+
+// One dense layer: out[j] = act(b[j] + sum_k W[j*NIN + k] in[k]) into the column.
+template <int NIN, bool STORE>
+__device__ __forceinline__ void dense_silu(const float *W, const float *bias, const float *in, float *col, float *zs,
+                                           float *as) {
+    const int T = blockDim.x;
+    for (int j = 0; j < NH; ++j) {
+        float s = bias[j];
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) s = fmaf(W[j * NIN + k], in[k], s);
+        const float a = silu(s);
+        col[j * T] = a;
+        if (STORE) { zs[j] = s; as[j] = a; }
+    }
+}
+
+// Forward pass of one sample (standardised features in f, standardised outputs).
+// With STORE, pre-activations z and activations a of the three hidden layers go
+// to zs/as ([3][64] each).
+template <bool STORE>
+__device__ __forceinline__ void forward(const Net &n, const float *f, float *out, float *zs, float *as) {
+    float *col = act_column();
+    const int T = blockDim.x;
+    float a[NH];
+    dense_silu<NI, STORE>(n.W1, n.b1, f, col, zs, as);
+#pragma unroll
+    for (int k = 0; k < NH; ++k) a[k] = col[k * T];
+    dense_silu<NH, STORE>(n.W2, n.b2, a, col, STORE ? zs + NH : nullptr, STORE ? as + NH : nullptr);
+#pragma unroll
+    for (int k = 0; k < NH; ++k) a[k] = col[k * T];
+    dense_silu<NH, STORE>(n.W3, n.b3, a, col, STORE ? zs + 2 * NH : nullptr, STORE ? as + 2 * NH : nullptr);
+#pragma unroll
+    for (int k = 0; k < NH; ++k) a[k] = col[k * T];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        float s = n.b4[o];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) s = fmaf(n.W4[o * NH + k], a[k], s);
+        out[o] = s;
+    }
+}
+
+// Learned start of step 1: Y^0_i = root of u = X_i + h(-u|u|^2 + 0.5 S_pred).
+__global__ void __launch_bounds__(128)
+k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__restrict__ blob,
+           const double *__restrict__ mom, int64_t N, int64_t Np, double h) {
+    extern __shared__ float smem[];
+    Net &n = *reinterpret_cast<Net *>(smem);
+    load_net(blob, n);
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double X[3];
+        float f[NI];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { X[c] = x[c * Np + i]; f[c] = (float)X[c]; }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) f[3 + k] = (float)mom[k];
+        f[15] = (float)h;
+#pragma unroll
+        for (int k = 0; k < NI; ++k) f[k] = (f[k] - n.fm[k]) / n.fs[k];
+        float o[NO];
+        forward<false>(n, f, o, nullptr, nullptr);
+        double S[3], u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { S[c] = (double)(o[c] * n.ys[c] + n.ym[c]); u[c] = X[c]; }
+        for (int it = 0; it < 30; ++it) {   // Newton on the cubic; Jacobian a I + 2h u u^T (Sherman-Morrison)
+            const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            double g[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c];
+            const double a = 1.0 + h * uu;
+            const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+            const double fct = 2.0 * h * ug / (a + 2.0 * h * uu);
+            double smax = 0.0, umax = 1.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double s = (g[c] - fct * u[c]) / a;
+                u[c] -= s;
+                smax = fmax(smax, fabs(s));
+                umax = fmax(umax, fabs(u[c]));
+            }
+            if (smax <= 1e-16 * umax) break;
+        }
+        if (isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[c * Np + i] = u[c];
+    }
+}
+
+// Network outputs (unstandardised) for raw feature rows (ssm_ws_predict).
+__global__ void __launch_bounds__(128)
+k_ws_predict(const float *__restrict__ blob, const float *__restrict__ feat, int64_t n_rows, float *__restrict__ out) {
+    extern __shared__ float smem[];
+    Net &n = *reinterpret_cast<Net *>(smem);
+    load_net(blob, n);
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += (int64_t)gridDim.x * blockDim.x) {
+        float f[NI], o[NO];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) f[k] = (feat[r * NI + k] - n.fm[k]) / n.fs[k];
+        forward<false>(n, f, o, nullptr, nullptr);
+#pragma unroll
+        for (int c = 0; c < NO; ++c) out[r * NO + c] = o[c] * n.ys[c] + n.ym[c];
+    }
+}
+
+// Training-data rows from the last step: X_n rebuilt from its converged root
+// (X = Y* - h v(Y*), exact up to the residual tolerance), the moments of X_n,
+// h, and the label S(Y*).
+__global__ void k_ws_collect(const double *__restrict__ y, const double *__restrict__ sconv,
+                             const double *__restrict__ mom_prev, int64_t N, int64_t Np, double h, int64_t stride,
+                             int64_t offset, int64_t rows, float *__restrict__ feat, float *__restrict__ label) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = offset + r * stride;
+        double Y[3], S[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { Y[c] = y[c * Np + i]; S[c] = sconv[c * Np + i]; }
+        const double yy = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            feat[r * NI + c] = (float)(Y[c] - h * (-Y[c] * yy + 0.5 * S[c]));
+            label[r * NO + c] = (float)S[c];
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) feat[r * NI + 3 + k] = (float)mom_prev[k];
+        feat[r * NI + 15] = (float)h;
+    }
+}
+
+// ---- training kernels -------------------------------------------------------
+// Per-sample buffers (row b of the batch): fz = standardised features [16],
+// Z = pre-activations [192], A = activations [192], D = deltas [192 + 3].
+
+__global__ void __launch_bounds__(128)
+k_train_fwd(const float *__restrict__ blob, const float *__restrict__ feat, const float *__restrict__ label,
+            const int *__restrict__ perm, int64_t b0, int B, float *__restrict__ FZ, float *__restrict__ Z,
+            float *__restrict__ A, float *__restrict__ D, double *__restrict__ loss) {
+    extern __shared__ float smem[];
+    Net &n = *reinterpret_cast<Net *>(smem);
+    load_net(blob, n);
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (b < B) {
+        const int64_t r = perm ? (int64_t)perm[b0 + b] : b0 + b;
+        float f[NI], o[NO];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            f[k] = (feat[r * NI + k] - n.fm[k]) / n.fs[k];
+            FZ[(int64_t)b * NI + k] = f[k];
+        }
+        forward<true>(n, f, o, Z + (int64_t)b * 3 * NH, A + (int64_t)b * 3 * NH);
+#pragma unroll
+        for (int c = 0; c < NO; ++c) {
+            const float t = (label[r * NO + c] - n.ym[c]) / n.ys[c];
+            const float e = o[c] - t;
+            l += (double)e * e;
+            D[(int64_t)b * (3 * NH + NO) + 3 * NH + c] = 2.0f * e / (float)(B * NO);   // d loss / d out
+        }
+    }
+    // block sum of the squared errors
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+    __shared__ double ws[4];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(loss, ws[0] + ws[1] + ws[2] + ws[3]);
+}
+
+__global__ void __launch_bounds__(128)
+k_train_bwd(const float *__restrict__ blob, int B, const float *__restrict__ Z, float *__restrict__ D) {
+    extern __shared__ float smem[];
+    Net &n = *reinterpret_cast<Net *>(smem);
+    load_net(blob, n);
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const float *z = Z + (int64_t)b * 3 * NH;
+    float *dl = D + (int64_t)b * (3 * NH + NO);
+    float g[NO], dv[NH];
+#pragma unroll
+    for (int c = 0; c < NO; ++c) g[c] = dl[3 * NH + c];
+    // delta of hidden layer 3: (W4^T g) * silu'(z3)
+    for (int k = 0; k < NH; ++k) {
+        float s = 0.f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) s = fmaf(n.W4[o * NH + k], g[o], s);
+        dl[2 * NH + k] = s * dsilu(z[2 * NH + k]);
+    }
+    // delta of layer 2 from layer 3 (through W3), then layer 1 from layer 2 (W2)
+#pragma unroll
+    for (int k = 0; k < NH; ++k) dv[k] = dl[2 * NH + k];
+    for (int k = 0; k < NH; ++k) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < NH; ++j) s = fmaf(n.W3[j * NH + k], dv[j], s);
+        dl[NH + k] = s * dsilu(z[NH + k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NH; ++k) dv[k] = dl[NH + k];
+    for (int k = 0; k < NH; ++k) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < NH; ++j) s = fmaf(n.W2[j * NH + k], dv[j], s);
+        dl[k] = s * dsilu(z[k]);
+    }
+}
+
+// Gradient of every parameter, summed over the batch in sample order (one
+// thread per parameter; deterministic).
+__global__ void __launch_bounds__(128)
+k_train_wgrad(int B, const float *__restrict__ FZ, const float *__restrict__ A, const float *__restrict__ D,
+              float *__restrict__ grad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NPARAM) return;
+    constexpr int DS = 3 * NH + NO;
+    int dj, in_k = -1, in_layer = -1;   // delta column, input column (-1: bias), input kind
+    if (p < P_B1) { dj = (p - P_W1) / NI; in_k = (p - P_W1) % NI; in_layer = 0; }
+    else if (p < P_W2) { dj = p - P_B1; }
+    else if (p < P_B2) { dj = NH + (p - P_W2) / NH; in_k = (p - P_W2) % NH; in_layer = 1; }
+    else if (p < P_W3) { dj = NH + (p - P_B2); }
+    else if (p < P_B3) { dj = 2 * NH + (p - P_W3) / NH; in_k = (p - P_W3) % NH; in_layer = 2; }
+    else if (p < P_W4) { dj = 2 * NH + (p - P_B3); }
+    else if (p < P_B4) { dj = 3 * NH + (p - P_W4) / NH; in_k = (p - P_W4) % NH; in_layer = 3; }
+    else { dj = 3 * NH + (p - P_B4); }
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) {
+        const float dv = D[(int64_t)b * DS + dj];
+        float av = 1.0f;
+        if (in_layer == 0) av = FZ[(int64_t)b * NI + in_k];
+        else if (in_layer > 0) av = A[(int64_t)b * 3 * NH + (in_layer - 1) * NH + in_k];
+        s = fmaf(dv, av, s);
+    }
+    grad[p] = s;
+}
+
+// Adam on the FP32 master weights; writes the BF16-rounded blob used by the forward.
+__global__ void k_adam(const float *__restrict__ grad, float *__restrict__ m, float *__restrict__ v,
+                       float *__restrict__ w, float *__restrict__ blob, float lr, float c1, float c2) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NPARAM) return;
+    const float g = grad[p];
+    const float mn = 0.9f * m[p] + 0.1f * g, vn = 0.999f * v[p] + 0.001f * g * g;
+    m[p] = mn;
+    v[p] = vn;
+    const float wn = w[p] - lr * (mn * c1) / (sqrtf(vn * c2) + 1e-8f);
+    w[p] = wn;
+    __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(blob + OFF_W);
+    if (p < P_B1) wb[p - P_W1] = __float2bfloat16_rn(wn);
+    else if (p < P_W2) blob[OFF_B1 + (p - P_B1)] = wn;
+    else if (p < P_B2) wb[NW1 + (p - P_W2)] = __float2bfloat16_rn(wn);
+    else if (p < P_W3) blob[OFF_B2 + (p - P_B2)] = wn;
+    else if (p < P_B3) wb[NW1 + NW2 + (p - P_W3)] = __float2bfloat16_rn(wn);
+    else if (p < P_W4) blob[OFF_B3 + (p - P_B3)] = wn;
+    else if (p < P_B4) wb[NW1 + NW2 + NW3 + (p - P_W4)] = __float2bfloat16_rn(wn);
+    else blob[OFF_B4 + (p - P_B4)] = wn;
+}
+
+constexpr size_t NET_SMEM = sizeof(Net) + sizeof(float) * NH * 128;   // net + activation columns (128 threads)
+
+bool blob_ok(const void *blob, size_t bytes) {
+    if (!blob || bytes < BLOB_BYTES) return false;
+    uint32_t h[2];
+    memcpy(h, blob, sizeof h);
+    return h[0] == WS_MAGIC && h[1] == WS_VERSION;
+}
+
+cudaError_t set_smem_limits() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_ws_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NET_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ws_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NET_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NET_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NET_SMEM);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t ws_forward_start(ssm_ctx *c) {
+    cudaError_t e = set_smem_limits();
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (c->N + 127) / 128;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+    return cudaGetLastError();
+}
+
+// splitmix64, for the host-side shuffles and initial weights of training.
+static uint64_t splitmix(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+static double unit(uint64_t &s) { return ((splitmix(s) >> 11) + 0.5) * 0x1p-53; }
+
+static uint16_t bf16_bits(float f) {   // round to nearest even
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// Host: fill a blob from master parameters and statistics.
+static void pack_blob(const std::vector<float> &w, const float *fm, const float *fs, const float *ym, const float *ys,
+                      std::vector<uint32_t> &blob) {
+    blob.assign(BLOB_WORDS, 0u);
+    blob[0] = WS_MAGIC; blob[1] = WS_VERSION; blob[2] = NI; blob[3] = NH; blob[4] = NO;
+    float *fb = reinterpret_cast<float *>(blob.data());
+    for (int k = 0; k < NI; ++k) { fb[OFF_FMEAN + k] = fm[k]; fb[OFF_FSTD + k] = fs[k]; }
+    for (int k = 0; k < 4; ++k) { fb[OFF_YMEAN + k] = k < NO ? ym[k] : 0.f; fb[OFF_YSTD + k] = k < NO ? ys[k] : 1.f; }
+    for (int k = 0; k < NH; ++k) { fb[OFF_B1 + k] = w[P_B1 + k]; fb[OFF_B2 + k] = w[P_B2 + k]; fb[OFF_B3 + k] = w[P_B3 + k]; }
+    for (int k = 0; k < NO; ++k) fb[OFF_B4 + k] = w[P_B4 + k];
+    uint16_t *wb = reinterpret_cast<uint16_t *>(fb + OFF_W);
+    for (int k = 0; k < NW1; ++k) wb[k] = bf16_bits(w[P_W1 + k]);
+    for (int k = 0; k < NW2; ++k) wb[NW1 + k] = bf16_bits(w[P_W2 + k]);
+    for (int k = 0; k < NW3; ++k) wb[NW1 + NW2 + k] = bf16_bits(w[P_W3 + k]);
+    for (int k = 0; k < NO * NH; ++k) wb[NW1 + NW2 + NW3 + k] = bf16_bits(w[P_W4 + k]);
+}
+
+// Host: master parameters of a blob (weights as their BF16 values).
+static void unpack_blob(const void *src, std::vector<float> &w) {
+    const float *fb = reinterpret_cast<const float *>(src);
+    const uint16_t *wb = reinterpret_cast<const uint16_t *>(fb + OFF_W);
+    auto f = [](uint16_t h) { uint32_t u = (uint32_t)h << 16; float v; memcpy(&v, &u, 4); return v; };
+    w.assign(NPARAM, 0.f);
+    for (int k = 0; k < NW1; ++k) w[P_W1 + k] = f(wb[k]);
+    for (int k = 0; k < NW2; ++k) w[P_W2 + k] = f(wb[NW1 + k]);
+    for (int k = 0; k < NW3; ++k) w[P_W3 + k] = f(wb[NW1 + NW2 + k]);
+    for (int k = 0; k < NO * NH; ++k) w[P_W4 + k] = f(wb[NW1 + NW2 + NW3 + k]);
+    for (int k = 0; k < NH; ++k) { w[P_B1 + k] = fb[OFF_B1 + k]; w[P_B2 + k] = fb[OFF_B2 + k]; w[P_B3 + k] = fb[OFF_B3 + k]; }
+    for (int k = 0; k < NO; ++k) w[P_B4 + k] = fb[OFF_B4 + k];
+}
+
 }  // namespace ssm
+
+using namespace ssm;
+
+namespace {
+ssm_status cst(cudaError_t e) {
+    return e == cudaSuccess ? SSM_OK : (e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA);
+}
+struct DevBuf {   // scoped device allocation for the training / checking entry points
+    void *p = nullptr;
+    cudaError_t alloc(size_t n) { return cudaMalloc(&p, n ? n : 1); }
+    ~DevBuf() { if (p) cudaFree(p); }
+    template <typename T> T *as() { return reinterpret_cast<T *>(p); }
+};
+}  // namespace
+
+extern "C" {
+
+size_t ssm_ws_blob_bytes(void) { return BLOB_BYTES; }
+
+ssm_status ssm_ws_load(ssm_ctx *c, const void *blob, size_t bytes) {
+    if (!c || !blob_ok(blob, bytes)) return SSM_EINVAL;
+    if (c->coef != SSM_COEF_COUPLED3D) return SSM_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(c->ws_w, blob, BLOB_BYTES, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cst(e);
+    c->ws_loaded = 1;
+    if (c->graph_ready) { cudaGraphExecDestroy(c->gexec); c->graph_ready = false; }
+    return SSM_OK;
+}
+
+ssm_status ssm_ws_collect(ssm_ctx *c, int64_t stride, int64_t offset, float *feat, float *label, int64_t *rows_out) {
+    if (!c || !feat || !label || stride < 1 || offset < 0 || c->coef != SSM_COEF_COUPLED3D) return SSM_EINVAL;
+    if (c->n < 1) return SSM_ESTATE;
+    const int64_t rows = offset < c->N ? (c->N - offset + stride - 1) / stride : 0;
+    if (rows_out) *rows_out = rows;
+    if (rows == 0) return SSM_OK;
+    DevBuf df, dl;
+    cudaError_t e = df.alloc(sizeof(float) * NI * rows);
+    if (e == cudaSuccess) e = dl.alloc(sizeof(float) * NO * rows);
+    if (e == cudaSuccess) {
+        const int64_t blocks = (rows + 255) / 256 < 1216 ? (rows + 255) / 256 : 1216;
+        k_ws_collect<<<(unsigned)blocks, 256, 0, c->st>>>(c->y, c->sconv, c->mom_prev, c->N, c->Np, c->h, stride,
+                                                          offset, rows, df.as<float>(), dl.as<float>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(feat, df.p, sizeof(float) * NI * rows, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(label, dl.p, sizeof(float) * NO * rows, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return cst(e);
+}
+
+ssm_status ssm_ws_predict(const void *blob, size_t bytes, const float *feat, int64_t n, float *out) {
+    if (!blob_ok(blob, bytes) || !feat || !out || n < 0) return SSM_EINVAL;
+    if (n == 0) return SSM_OK;
+    DevBuf db, df, dout;
+    cudaError_t e = set_smem_limits();
+    if (e == cudaSuccess) e = db.alloc(BLOB_BYTES);
+    if (e == cudaSuccess) e = df.alloc(sizeof(float) * NI * n);
+    if (e == cudaSuccess) e = dout.alloc(sizeof(float) * NO * n);
+    if (e == cudaSuccess) e = cudaMemcpy(db.p, blob, BLOB_BYTES, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(df.p, feat, sizeof(float) * NI * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int64_t blocks = (n + 127) / 128 < 1216 ? (n + 127) / 128 : 1216;
+        k_ws_predict<<<(unsigned)blocks, 128, NET_SMEM>>>(db.as<float>(), df.as<float>(), n, dout.as<float>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout.p, sizeof(float) * NO * n, cudaMemcpyDeviceToHost);
+    return cst(e);
+}
+
+// One forward + backward over n rows with the blob's weights: the gradient of the
+// mean squared error of the standardised outputs w.r.t. the parameters, in the
+// order W1 [64x16], b1, W2 [64x64], b2, W3 [64x64], b3, W4 [3x64], b4.
+ssm_status ssm_ws_grad(const void *blob, size_t bytes, const float *feat, const float *label, int64_t n,
+                       float *grad, double *loss) {
+    if (!blob_ok(blob, bytes) || !feat || !label || !grad || n < 1 || n > (1 << 20)) return SSM_EINVAL;
+    DevBuf db, df, dl, fz, z, a, d, g, ls;
+    const int B = (int)n;
+    cudaError_t e = set_smem_limits();
+    if (e == cudaSuccess) e = db.alloc(BLOB_BYTES);
+    if (e == cudaSuccess) e = df.alloc(sizeof(float) * NI * n);
+    if (e == cudaSuccess) e = dl.alloc(sizeof(float) * NO * n);
+    if (e == cudaSuccess) e = fz.alloc(sizeof(float) * NI * n);
+    if (e == cudaSuccess) e = z.alloc(sizeof(float) * 3 * NH * n);
+    if (e == cudaSuccess) e = a.alloc(sizeof(float) * 3 * NH * n);
+    if (e == cudaSuccess) e = d.alloc(sizeof(float) * (3 * NH + NO) * n);
+    if (e == cudaSuccess) e = g.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = ls.alloc(sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(db.p, blob, BLOB_BYTES, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(df.p, feat, sizeof(float) * NI * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dl.p, label, sizeof(float) * NO * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ls.p, 0, sizeof(double));
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((n + 127) / 128);
+        k_train_fwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), df.as<float>(), dl.as<float>(), nullptr, 0, B,
+                                               fz.as<float>(), z.as<float>(), a.as<float>(), d.as<float>(), ls.as<double>());
+        k_train_bwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), B, z.as<float>(), d.as<float>());
+        k_train_wgrad<<<(NPARAM + 127) / 128, 128>>>(B, fz.as<float>(), a.as<float>(), d.as<float>(), g.as<float>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(grad, g.p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost);
+    double l = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpy(&l, ls.p, sizeof(double), cudaMemcpyDeviceToHost);
+    if (loss) *loss = l / (double)(n * NO);
+    return cst(e);
+}
+
+// Train the network on n rows (features [n][16], labels [n][3], host arrays):
+// minibatch Adam, `epochs` passes over a fresh random order each, learning rate
+// lr decayed by a cosine to lr/20, initial weights N(0, 1/fan_in) from `seed`.
+// Writes the blob (ssm_ws_blob_bytes() bytes) and, if loss_curve != NULL, the
+// mean training loss of each epoch.  Synchronous; allocates its own device buffers.
+ssm_status ssm_ws_train(const float *feat, const float *label, int64_t n, int epochs, int batch, float lr,
+                        uint64_t seed, void *blob_out, size_t bytes, double *loss_curve) {
+    if (!feat || !label || !blob_out || bytes < BLOB_BYTES || n < 2 || epochs < 1 || batch < 1 ||
+        batch > (1 << 16) || n > ((int64_t)1 << 28) || !(lr > 0.f))
+        return SSM_EINVAL;
+    // feature / label statistics (host, double)
+    float fm[NI], fs[NI], ym[NO], ys[NO];
+    for (int k = 0; k < NI; ++k) {
+        double s = 0, s2 = 0;
+        for (int64_t r = 0; r < n; ++r) { const double v = feat[r * NI + k]; s += v; s2 += v * v; }
+        const double m = s / n, var = s2 / n - m * m;
+        fm[k] = (float)m;
+        fs[k] = (float)(var > 1e-20 ? sqrt(var) : 1.0);
+    }
+    for (int k = 0; k < NO; ++k) {
+        double s = 0, s2 = 0;
+        for (int64_t r = 0; r < n; ++r) { const double v = label[r * NO + k]; s += v; s2 += v * v; }
+        const double m = s / n, var = s2 / n - m * m;
+        ym[k] = (float)m;
+        ys[k] = (float)(var > 1e-20 ? sqrt(var) : 1.0);
+    }
+    // initial weights
+    uint64_t rs = seed ^ 0x5353574E45540001ull;
+    std::vector<float> w(NPARAM, 0.f);
+    auto gauss = [&]() { const double u1 = unit(rs), u2 = unit(rs); return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2); };
+    for (int k = 0; k < NW1; ++k) w[P_W1 + k] = (float)(gauss() / sqrt((double)NI));
+    for (int k = 0; k < NW2; ++k) w[P_W2 + k] = (float)(gauss() / sqrt((double)NH));
+    for (int k = 0; k < NW3; ++k) w[P_W3 + k] = (float)(gauss() / sqrt((double)NH));
+    for (int k = 0; k < NO * NH; ++k) w[P_W4 + k] = (float)(gauss() / sqrt((double)NH));
+    std::vector<uint32_t> blob;
+    pack_blob(w, fm, fs, ym, ys, blob);
+
+    const int B = batch;
+    DevBuf db, df, dl, dperm, fz, z, a, d, g, m, v, dw, ls;
+    cudaError_t e = set_smem_limits();
+    if (e == cudaSuccess) e = db.alloc(BLOB_BYTES);
+    if (e == cudaSuccess) e = df.alloc(sizeof(float) * NI * n);
+    if (e == cudaSuccess) e = dl.alloc(sizeof(float) * NO * n);
+    if (e == cudaSuccess) e = dperm.alloc(sizeof(int) * n);
+    if (e == cudaSuccess) e = fz.alloc(sizeof(float) * NI * B);
+    if (e == cudaSuccess) e = z.alloc(sizeof(float) * 3 * NH * B);
+    if (e == cudaSuccess) e = a.alloc(sizeof(float) * 3 * NH * B);
+    if (e == cudaSuccess) e = d.alloc(sizeof(float) * (3 * NH + NO) * B);
+    if (e == cudaSuccess) e = g.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = m.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = v.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = dw.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = ls.alloc(sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(db.p, blob.data(), BLOB_BYTES, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(df.p, feat, sizeof(float) * NI * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dl.p, label, sizeof(float) * NO * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dw.p, w.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m.p, 0, sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = cudaMemset(v.p, 0, sizeof(float) * NPARAM);
+    std::vector<int> perm((size_t)n);
+    const int64_t nb = n / B > 0 ? n / B : 1;
+    const int Bl = n < B ? (int)n : B;
+    int64_t step = 0;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        for (int64_t r = 0; r < n; ++r) perm[r] = (int)r;
+        for (int64_t r = n - 1; r > 0; --r) {   // Fisher-Yates
+            const int64_t j = (int64_t)(splitmix(rs) % (uint64_t)(r + 1));
+            const int t = perm[r]; perm[r] = perm[j]; perm[j] = t;
+        }
+        e = cudaMemcpy(dperm.p, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(ls.p, 0, sizeof(double));
+        for (int64_t bi = 0; bi < nb && e == cudaSuccess; ++bi, ++step) {
+            const double prog = (double)(ep * nb + bi) / (double)(epochs * nb);
+            const float lr_t = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + cos(3.141592653589793 * prog))));
+            const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)(step + 1))));
+            const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)(step + 1))));
+            const unsigned blocks = (unsigned)((Bl + 127) / 128);
+            k_train_fwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), df.as<float>(), dl.as<float>(), dperm.as<int>(),
+                                                   bi * Bl, Bl, fz.as<float>(), z.as<float>(), a.as<float>(),
+                                                   d.as<float>(), ls.as<double>());
+            k_train_bwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), Bl, z.as<float>(), d.as<float>());
+            k_train_wgrad<<<(NPARAM + 127) / 128, 128>>>(Bl, fz.as<float>(), a.as<float>(), d.as<float>(), g.as<float>());
+            k_adam<<<(NPARAM + 127) / 128, 128>>>(g.as<float>(), m.as<float>(), v.as<float>(), dw.as<float>(),
+                                                  db.as<float>(), lr_t, c1, c2);
+            e = cudaGetLastError();
+        }
+        double l = 0.0;
+        if (e == cudaSuccess) e = cudaMemcpy(&l, ls.p, sizeof(double), cudaMemcpyDeviceToHost);
+        if (loss_curve) loss_curve[ep] = l / (double)(nb * Bl * NO);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(blob_out, db.p, BLOB_BYTES, cudaMemcpyDeviceToHost);
+    return cst(e);
+}
+
+// Host helper for tests: the parameter vector (weights at their BF16 values) of a blob.
+ssm_status ssm_ws_params(const void *blob, size_t bytes, float *params) {
+    if (!blob_ok(blob, bytes) || !params) return SSM_EINVAL;
+    std::vector<float> w;
+    unpack_blob(blob, w);
+    memcpy(params, w.data(), sizeof(float) * NPARAM);
+    return SSM_OK;
+}
+
+int ssm_ws_num_params(void) { return NPARAM; }
+
+}  // extern "C"

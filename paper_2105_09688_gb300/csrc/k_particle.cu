@@ -181,9 +181,12 @@ k_ou_implicit(const double *x, double *y, int64_t N, int64_t Np, double inv, dou
 // Sherman-Morrison inverts in closed form; a few Newton steps solve it to
 // rounding.  The outer iteration contracts by about 0.5 h |(2 w^2 d d^T)| per pass.
 // ---------------------------------------------------------------------------
+// Plain start Y = X (a learned start, when enabled, overwrites Y afterwards);
+// resets the active list, pass counters and histogram, and keeps the moments of
+// X_n that the learned start and the training-data collection use.
 __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
                                int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
-                               int64_t N, int64_t Np) {
+                               const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
 #pragma unroll
@@ -195,6 +198,7 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
         cnt[0] = (int)N;
         for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
         for (int k = 0; k < 16; ++k) hist[k] = 0;
+        for (int k = 0; k < 12; ++k) mom_prev[k] = mom[k];
     }
 }
 
@@ -202,9 +206,12 @@ __global__ void __launch_bounds__(256)
 k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int *__restrict__ act_in,
                 const int *__restrict__ cnt_in, int *__restrict__ act_out, int *__restrict__ cnt_out,
                 const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h, double tol,
-                int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err) {
+                int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err,
+                double *__restrict__ sconv, int restart_pass, long long *counters) {
     __shared__ int bh[16];
+    __shared__ int nrestart;
     if (threadIdx.x < 16) bh[threadIdx.x] = 0;
+    if (threadIdx.x == 0) nrestart = 0;
     __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n_in = *cnt_in;
@@ -246,9 +253,18 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
         if (rinf <= tol) {
             passes[i] = pass + 1;
             atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
-        } else if (pass + 1 >= kmax || !(rinf == rinf)) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sconv[c * Np + i] = S[c];
+        } else if (pass + 1 >= kmax || !(rinf == rinf && fabs(Y[0]) + fabs(Y[1]) + fabs(Y[2]) < 1e300)) {
             passes[i] = pass + 1;
             atomicOr(err, rinf == rinf ? ERR_NOCONV : ERR_NONFINITE);
+        } else if (pass + 1 == restart_pass) {
+            // A learned start that has not converged after restart_pass passes:
+            // fall back to the plain start Y = X and continue with plain passes.
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[c * Np + i] = X[c];
+            atomicAdd(&nrestart, 1);
+            keep = true;
         } else {
             double u[3] = { Y[0], Y[1], Y[2] };
             for (int it = 0; it < 30; ++it) {
@@ -286,6 +302,8 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
     }
     __syncthreads();
     if (threadIdx.x < 16 && bh[threadIdx.x]) atomicAdd((unsigned long long *)&hist[threadIdx.x], (unsigned long long)bh[threadIdx.x]);
+    if (threadIdx.x == 0 && nrestart)
+        atomicAdd((unsigned long long *)&counters[CNT_FALLBACKS], (unsigned long long)nrestart);
 }
 
 // Work counters of one implicit step (one thread).
@@ -465,14 +483,17 @@ cudaError_t launch_ou_implicit(ssm_ctx *c) {
 }
 
 cudaError_t launch_newton_begin(ssm_ctx *c) {
-    k_newton_begin<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist, c->N, c->Np);
+    k_newton_begin<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
+                                                       c->mom, c->mom_prev, c->N, c->Np);
     return cudaGetLastError();
 }
 
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32) {
     k_newton_update<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, c->cnt + pass + 1,
                                                         c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32,
-                                                        pass, c->kmax, c->passes, c->hist, c->err);
+                                                        pass, c->kmax, c->passes, c->hist, c->err, c->sconv,
+                                                        (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1,
+                                                        c->counters);
     return cudaGetLastError();
 }
 
