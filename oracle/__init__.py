@@ -16,6 +16,7 @@ from .build import build_oracle
 COEF_CUBIC1D_GAUSS = 0
 COEF_COUPLED3D = 1
 COEF_OU = 2
+COEF_COUPLED1D = 3
 
 _c_int, _c_i64, _c_dbl, _c_u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
 
@@ -155,11 +156,12 @@ def drift_one(P, y, i):
 
 def pair_sum_coupled(P, x, y_point):
     x = _c(x, P)
-    yp = np.ascontiguousarray(y_point, dtype=np.float64).reshape(3)
+    yp = np.zeros(3)
+    yp[:P.d] = np.asarray(y_point, dtype=np.float64).reshape(P.d)
     S = np.empty(3)
     JS = np.empty(9)
     lib().orc_pair_sum_coupled(ctypes.byref(P), _dp(x), _dp(yp), _dp(S), _dp(JS))
-    return S, JS.reshape(3, 3)
+    return S[:P.d].copy(), JS[:P.d * P.d].reshape(P.d, P.d)
 
 
 def implicit_step(P, x):

@@ -30,6 +30,7 @@
  *     v(y, mu) = -y|y|^2 + 0.5 * int (z - y) / (1 + |y - z|^2) mu(dz),
  *     b(y, mu) = int (z - y) exp(-|y - z|^2 / 2) mu(dz),
  *     sigma(y) = diag(0.3 y_k + 0.2).
+ *   ORC_COEF_COUPLED1D: the same three formulas at d = 1.
  *   ORC_COEF_OU, any d (componentwise), §3.4.1 Eq. (stablity:OU):
  *     v(x) = rho x,  b(mu) = lambda * int z mu(dz),  sigma = eta.
  *
@@ -37,9 +38,9 @@
  *   CUBIC1D_GAUSS: h y^3 + (1 - h) y - x = 0 has exactly one real root for
  *     0 < h < 1 (Lemma 4.1 with L_v = 1).  Cardano's formula in a
  *     cancellation-free form, then one Newton correction.
- *   COUPLED3D: Newton's method on F(y) = y - x - h v(y, mu^X) with the exact
- *     3x3 Jacobian, Gaussian elimination with partial pivoting, step halving
- *     when the residual grows, start y = x.
+ *   COUPLED3D / COUPLED1D: Newton's method on F(y) = y - x - h v(y, mu^X) with
+ *     the exact d x d Jacobian, Gaussian elimination with partial pivoting, step
+ *     halving when the residual grows, start y = x.
  *   OU: y = x / (1 - h rho) (Remark 4.3 gives this closed form for v = a x).
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
@@ -165,17 +166,15 @@ static void drift_b(const orc_problem *P, const double *y, const double *yi, dou
             s += dz * exp(-(dz * dz));
         }
         b[0] = 0.5 * (s / (double)N);
-    } else if (P->coef == ORC_COEF_COUPLED3D) {
+    } else if (P->coef == ORC_COEF_COUPLED3D || P->coef == ORC_COEF_COUPLED1D) {
         double s[3] = { 0.0, 0.0, 0.0 };
         for (int64_t j = 0; j < N; ++j) {
-            double d0 = y[3 * j + 0] - yi[0];
-            double d1 = y[3 * j + 1] - yi[1];
-            double d2 = y[3 * j + 2] - yi[2];
-            double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            double dd[3], r2 = 0.0;
+            for (int c = 0; c < d; ++c) { dd[c] = y[(int64_t)d * j + c] - yi[c]; r2 += dd[c] * dd[c]; }
             double e = exp(-r2 / 2.0);
-            s[0] += d0 * e; s[1] += d1 * e; s[2] += d2 * e;
+            for (int c = 0; c < d; ++c) s[c] += dd[c] * e;
         }
-        for (int c = 0; c < 3; ++c) b[c] = s[c] / (double)N;
+        for (int c = 0; c < d; ++c) b[c] = s[c] / (double)N;
     } else { /* OU: lambda * mean */
         for (int c = 0; c < d; ++c) {
             double s = 0.0;
@@ -190,89 +189,96 @@ static void diffusion_times_dw(const orc_problem *P, const double *yi, const dou
     const int d = P->d;
     if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
         out[0] = (0.4 * yi[0] + 0.1) * dw[0];
-    } else if (P->coef == ORC_COEF_COUPLED3D) {
-        for (int c = 0; c < 3; ++c) out[c] = (0.3 * yi[c] + 0.2) * dw[c];
+    } else if (P->coef == ORC_COEF_COUPLED3D || P->coef == ORC_COEF_COUPLED1D) {
+        for (int c = 0; c < d; ++c) out[c] = (0.3 * yi[c] + 0.2) * dw[c];
     } else {
         for (int c = 0; c < d; ++c) out[c] = P->p[2] * dw[c];
     }
 }
 
-/* Pair part of v for COUPLED3D at the point y against mu^X:
+/* Pair part of v for the coupled sets (d = 3 or 1) at the point y against mu^X:
  *   S(y)  = (1/N) sum_j (x_j - y) w_j,  w_j = 1 / (1 + |x_j - y|^2)
- *   JS(y) = dS/dy = (1/N) sum_j ( -w_j I + 2 w_j^2 (x_j - y)(x_j - y)^T ). */
+ *   JS(y) = dS/dy = (1/N) sum_j ( -w_j I + 2 w_j^2 (x_j - y)(x_j - y)^T ).
+ * JS is d x d, row-major. */
 static void pair_sum_coupled(const orc_problem *P, const double *x, const double *y,
                              double S[3], double JS[9])
 {
     const int64_t N = P->N;
+    const int d = P->d;
     double s[3] = { 0, 0, 0 };
     double j9[9] = { 0, 0, 0, 0, 0, 0, 0, 0, 0 };
     for (int64_t j = 0; j < N; ++j) {
-        double dd[3] = { x[3 * j] - y[0], x[3 * j + 1] - y[1], x[3 * j + 2] - y[2] };
-        double w = 1.0 / (1.0 + dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        for (int a = 0; a < 3; ++a) {
+        double dd[3] = { 0, 0, 0 }, q = 1.0;
+        for (int a = 0; a < d; ++a) dd[a] = x[(int64_t)d * j + a] - y[a];
+        for (int a = 0; a < d; ++a) q += dd[a] * dd[a];
+        double w = 1.0 / q;
+        for (int a = 0; a < d; ++a) {
             s[a] += dd[a] * w;
-            for (int c = 0; c < 3; ++c)
-                j9[3 * a + c] += (a == c ? -w : 0.0) + 2.0 * w * w * dd[a] * dd[c];
+            for (int c = 0; c < d; ++c)
+                j9[d * a + c] += (a == c ? -w : 0.0) + 2.0 * w * w * dd[a] * dd[c];
         }
     }
-    for (int a = 0; a < 3; ++a) S[a] = s[a] / (double)N;
+    for (int a = 0; a < d; ++a) S[a] = s[a] / (double)N;
     if (JS)
-        for (int k = 0; k < 9; ++k) JS[k] = j9[k] / (double)N;
+        for (int k = 0; k < d * d; ++k) JS[k] = j9[k] / (double)N;
 }
 
-/* Residual F(y) = y - x_i - h v(y, mu^X) for COUPLED3D, and optionally its Jacobian. */
+/* Residual F(y) = y - x_i - h v(y, mu^X) for the coupled sets, and optionally its
+ * Jacobian (d x d, row-major). */
 static void coupled_residual(const orc_problem *P, const double *x, const double *xi,
                              const double *y, double F[3], double J[9])
 {
+    const int d = P->d;
     double S[3], JS[9];
     pair_sum_coupled(P, x, y, S, J ? JS : NULL);
-    double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-    for (int a = 0; a < 3; ++a) {
+    double r2 = 0.0;
+    for (int a = 0; a < d; ++a) r2 += y[a] * y[a];
+    for (int a = 0; a < d; ++a) {
         double v = -y[a] * r2 + 0.5 * S[a];
         F[a] = y[a] - xi[a] - P->h * v;
     }
     if (J) {
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) {
+        for (int a = 0; a < d; ++a)
+            for (int c = 0; c < d; ++c) {
                 /* dv_a/dy_c = -(r2 delta_ac + 2 y_a y_c) + 0.5 JS_ac */
-                double dv = -((a == c ? r2 : 0.0) + 2.0 * y[a] * y[c]) + 0.5 * JS[3 * a + c];
-                J[3 * a + c] = (a == c ? 1.0 : 0.0) - P->h * dv;
+                double dv = -((a == c ? r2 : 0.0) + 2.0 * y[a] * y[c]) + 0.5 * JS[d * a + c];
+                J[d * a + c] = (a == c ? 1.0 : 0.0) - P->h * dv;
             }
     }
 }
 
-/* Solve the 3x3 system A s = r by Gaussian elimination with partial pivoting. */
-static int solve3(const double A_in[9], const double r_in[3], double s[3])
+/* Solve the d x d system A s = r (d <= 3) by Gaussian elimination with partial pivoting. */
+static int solve_small(int d, const double *A_in, const double *r_in, double *s)
 {
     double A[3][4];
-    for (int a = 0; a < 3; ++a) {
-        for (int c = 0; c < 3; ++c) A[a][c] = A_in[3 * a + c];
-        A[a][3] = r_in[a];
+    for (int a = 0; a < d; ++a) {
+        for (int c = 0; c < d; ++c) A[a][c] = A_in[d * a + c];
+        A[a][d] = r_in[a];
     }
-    for (int col = 0; col < 3; ++col) {
+    for (int col = 0; col < d; ++col) {
         int piv = col;
-        for (int row = col + 1; row < 3; ++row)
+        for (int row = col + 1; row < d; ++row)
             if (fabs(A[row][col]) > fabs(A[piv][col])) piv = row;
         if (A[piv][col] == 0.0) return -1;
         if (piv != col)
-            for (int c = 0; c < 4; ++c) { double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t; }
-        for (int row = col + 1; row < 3; ++row) {
+            for (int c = 0; c <= d; ++c) { double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t; }
+        for (int row = col + 1; row < d; ++row) {
             double f = A[row][col] / A[col][col];
-            for (int c = col; c < 4; ++c) A[row][c] -= f * A[col][c];
+            for (int c = col; c <= d; ++c) A[row][c] -= f * A[col][c];
         }
     }
-    for (int row = 2; row >= 0; --row) {
-        double acc = A[row][3];
-        for (int c = row + 1; c < 3; ++c) acc -= A[row][c] * s[c];
+    for (int row = d - 1; row >= 0; --row) {
+        double acc = A[row][d];
+        for (int c = row + 1; c < d; ++c) acc -= A[row][c] * s[c];
         s[row] = acc / A[row][row];
     }
     return 0;
 }
 
-static double norminf3(const double *v) {
-    double m = fabs(v[0]);
-    if (fabs(v[1]) > m) m = fabs(v[1]);
-    if (fabs(v[2]) > m) m = fabs(v[2]);
+static double norminf(int d, const double *v) {
+    double m = 0.0;
+    for (int c = 0; c < d; ++c)
+        if (fabs(v[c]) > m) m = fabs(v[c]);
     return m;
 }
 
@@ -313,30 +319,31 @@ int orc_implicit_point(const orc_problem *P, const double *x, const double *xi, 
         for (int c = 0; c < d; ++c) y_out[c] = xi[c] / (1.0 - P->h * P->p[0]);
         return 0;
     }
-    /* COUPLED3D: damped Newton from y = x_i. */
-    double y[3] = { xi[0], xi[1], xi[2] };
+    /* coupled sets: damped Newton from y = x_i. */
+    double y[3] = { 0, 0, 0 };
+    for (int a = 0; a < d; ++a) y[a] = xi[a];
     double F[3], J[9], s[3];
     coupled_residual(P, x, xi, y, F, J);
     for (int it = 1; it <= 50; ++it) {
-        if (solve3(J, F, s) != 0) return -1;
-        double fn = norminf3(F);
-        double lam = 1.0, yt[3], Ft[3], Jt[9];
+        if (solve_small(d, J, F, s) != 0) return -1;
+        double fn = norminf(d, F);
+        double lam = 1.0, yt[3] = { 0, 0, 0 }, Ft[3], Jt[9];
         for (int half = 0; half < 40; ++half) {
-            for (int a = 0; a < 3; ++a) yt[a] = y[a] - lam * s[a];
+            for (int a = 0; a < d; ++a) yt[a] = y[a] - lam * s[a];
             coupled_residual(P, x, xi, yt, Ft, Jt);
-            if (norminf3(Ft) <= fn || half == 39) break;
+            if (norminf(d, Ft) <= fn || half == 39) break;
             lam *= 0.5;
         }
-        double step = lam * norminf3(s);
-        for (int a = 0; a < 3; ++a) { y[a] = yt[a]; F[a] = Ft[a]; }
+        double step = lam * norminf(d, s);
+        for (int a = 0; a < d; ++a) { y[a] = yt[a]; F[a] = Ft[a]; }
         memcpy(J, Jt, sizeof J);
-        double scale = norminf3(y) > 1.0 ? norminf3(y) : 1.0;
+        double scale = norminf(d, y) > 1.0 ? norminf(d, y) : 1.0;
         if (step <= 1e-14 * scale) {
-            for (int a = 0; a < 3; ++a) y_out[a] = y[a];
+            for (int a = 0; a < d; ++a) y_out[a] = y[a];
             return it;
         }
     }
-    for (int a = 0; a < 3; ++a) y_out[a] = y[a];
+    for (int a = 0; a < d; ++a) y_out[a] = y[a];
     return -1;
 }
 

@@ -14,7 +14,7 @@
 
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_COEF_CUBIC1D_GAUSS = 0, ORC_COEF_COUPLED3D = 1, ORC_COEF_OU = 2 };
+enum { ORC_COEF_CUBIC1D_GAUSS = 0, ORC_COEF_COUPLED3D = 1, ORC_COEF_OU = 2, ORC_COEF_COUPLED1D = 3 };
 
 typedef struct {
     int d;            /* space dimension: 1 or 3 (OU: any) */

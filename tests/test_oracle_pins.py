@@ -102,7 +102,8 @@ def test_linear_implicit_remark():
 
 
 @pytest.mark.parametrize("coef,d,Lv", [(O.COEF_CUBIC1D_GAUSS, 1, 1.0),
-                                       (O.COEF_COUPLED3D, 3, 1.0 / 16.0)])
+                                       (O.COEF_COUPLED3D, 3, 1.0 / 16.0),
+                                       (O.COEF_COUPLED1D, 1, 1.0 / 16.0)])
 def test_lemma_4_1_inequalities(coef, d, Lv):
     """Lemma 4.1 (4.1), (4.2), (4.5) for the implicit map F_h with a frozen measure.
 
@@ -141,7 +142,7 @@ def test_lemma_4_1_inequalities(coef, d, Lv):
 # Pairwise interaction: invariants
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("coef,d", [(O.COEF_CUBIC1D_GAUSS, 1), (O.COEF_COUPLED3D, 3)])
+@pytest.mark.parametrize("coef,d", [(O.COEF_CUBIC1D_GAUSS, 1), (O.COEF_COUPLED3D, 3), (O.COEF_COUPLED1D, 1)])
 def test_drift_is_antisymmetric_and_translation_invariant(coef, d):
     """sum_i b(Y_i, mu^Y) = 0 (antisymmetric pair kernel, self term zero) and
     b(Y + c, mu^{Y + c}) = b(Y, mu^Y)."""
@@ -191,13 +192,13 @@ def _brute_step(mp, coef, x, dw, h):
     def v(yi):
         if coef == O.COEF_CUBIC1D_GAUSS:
             return [yi[0] - yi[0] ** 3]
-        s = [mp.mpf(0)] * 3
+        s = [mp.mpf(0)] * d
         for xj in X:
-            dd = [xj[c] - yi[c] for c in range(3)]
+            dd = [xj[c] - yi[c] for c in range(d)]
             w = 1 / (1 + sum(t * t for t in dd))
-            s = [s[c] + dd[c] * w for c in range(3)]
+            s = [s[c] + dd[c] * w for c in range(d)]
         r2 = sum(t * t for t in yi)
-        return [-yi[c] * r2 + s[c] / (2 * N) for c in range(3)]
+        return [-yi[c] * r2 + s[c] / (2 * N) for c in range(d)]
 
     Y = []
     for xi in X:
@@ -222,14 +223,15 @@ def _brute_step(mp, coef, x, dw, h):
             b = [mp.mpf("0.5") * s[0] / N]
             sig = [mp.mpf("0.4") * yi[0] + mp.mpf("0.1")]
         else:
-            b = [s[c] / N for c in range(3)]
-            sig = [mp.mpf("0.3") * yi[c] + mp.mpf("0.2") for c in range(3)]
+            b = [s[c] / N for c in range(d)]
+            sig = [mp.mpf("0.3") * yi[c] + mp.mpf("0.2") for c in range(d)]
         out.append([yi[c] + H * b[c] + sig[c] * mp.mpf(float(dw[i][c])) for c in range(d)])
     return np.array([[float(t) for t in r] for r in Y]), np.array([[float(t) for t in r] for r in out])
 
 
 @pytest.mark.parametrize("coef,d,N", [(O.COEF_CUBIC1D_GAUSS, 1, 7), (O.COEF_COUPLED3D, 3, 5),
-                                      (O.COEF_COUPLED3D, 3, 1), (O.COEF_CUBIC1D_GAUSS, 1, 2)])
+                                      (O.COEF_COUPLED3D, 3, 1), (O.COEF_CUBIC1D_GAUSS, 1, 2),
+                                      (O.COEF_COUPLED1D, 1, 6)])
 def test_whole_step_matches_high_precision_brute_force(coef, d, N):
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
