@@ -60,8 +60,9 @@ typedef enum {
  *      solved by Newton-type iterations whose N^2 pair sums run on the GPU.
  *  SSM_COEF_OU (any d, componentwise; §3.4.1 Eq. (stablity:OU)): v(x) = rho x,
  *      b(mu) = lambda int z mu(dz), sigma = eta, with (rho, lambda, eta) taken
- *      from ssm_opts.coef_params[0..2]. */
-typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2 } ssm_coef;
+ *      from ssm_opts.coef_params[0..2].
+ *  SSM_COEF_COUPLED1D (d = 1): the three formulas of SSM_COEF_COUPLED3D at d = 1. */
+typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2, SSM_COEF_COUPLED1D = 3 } ssm_coef;
 
 /* Arithmetic of the O(N^2) pair sums.
  *  SSM_FP64: IEEE double throughout.
@@ -204,6 +205,64 @@ ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
  * targets per thread}; the chunk count is planned as in ssm_autotune.
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
+
+/* ---- batched form: many independent ensembles in one graph launch ----
+ * Each ensemble is the coupled coefficient set (SSM_COEF_COUPLED3D formulas) at
+ * d = 1 or d = 3, with its own N, h, T, seed and Brownian grid, stepped by the SSM
+ * of §2.3 exactly as a single context would step it (same kernels' device code,
+ * same Philox streams): results match ssm_create/ssm_run of each ensemble alone to
+ * rounding of the pair-sum grouping.  One batch step advances every unfinished
+ * ensemble by one step; ensembles with fewer steps (larger h) stop early.  The
+ * whole run is one CUDA graph with device-side loops over steps and over the
+ * passes of step 1 (graph conditional nodes), so ssm_batch_run is a single
+ * graph launch.  Precision SSM_FP64 or SSM_FP32C (ssm_opts.precision); the other
+ * ssm_opts fields used are newton_tol, newton_kmax, x0_mean, x0_std, stream. */
+typedef struct {
+    int d;              /* 1 or 3 */
+    int64_t N;          /* particles, 1 .. 2^24 */
+    double h, T;        /* step size and horizon (M = T/h steps; h <= 1/(1 + 2/16)) */
+    uint64_t seed;      /* Philox key of X_0 and dW */
+    int fine_log2;      /* 0: dW on the ensemble's own grid; L > 0: Brownian path on the grid T 2^-L */
+} ssm_ens_desc;
+
+typedef struct ssm_batch ssm_batch;
+
+/* Create n <= 1024 ensembles (descriptors desc[n], host) and draw their X_0.
+ * SSM_EINVAL for a bad descriptor (same rules as ssm_create).  Synchronous. */
+ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opts, ssm_batch **out);
+
+/* Enqueue up to k batch steps (one graph launch; stops early when every ensemble
+ * has reached its horizon).  Asynchronous. */
+ssm_status ssm_batch_run_steps(ssm_batch *b, int64_t k);
+
+/* Enqueue the whole run: every ensemble to its horizon, one graph launch. */
+ssm_status ssm_batch_run(ssm_batch *b);
+
+/* Wait and report device-detected errors (sticky, as for contexts). */
+ssm_status ssm_batch_sync(ssm_batch *b);
+
+/* State of ensemble e (host x[N*d], particle-major) and its step index. Synchronising. */
+ssm_status ssm_batch_get_state(ssm_batch *b, int e, double *x, int64_t *n);
+
+/* Raw moments of ensemble e, out[k*d + c], k = 0..3.  Synchronising. */
+ssm_status ssm_batch_moments(ssm_batch *b, int e, double *out);
+
+/* Work counters summed over ensembles (steps = ensemble-steps; max_passes holds
+ * the number of batch steps taken).  Synchronising. */
+ssm_status ssm_batch_stats(ssm_batch *b, ssm_stats_t *out);
+
+/* Autotuner (no counterpart in the paper): times each compiled launch shape and
+ * source-chunk length on the batch's pair-sum phases and rebuilds the graph with
+ * the fastest; *best_ms = the best time of one step-1 pass plus one drift pass
+ * over all ensembles.  Leaves the state unchanged.  Synchronising. */
+ssm_status ssm_batch_autotune(ssm_batch *b, double *best_ms);
+
+/* Launch shape in use: out[5] = {packed d=3 kernel, threads, targets/thread d=1,
+ * targets/thread d=3, sources per chunk}. */
+ssm_status ssm_batch_get_plan(ssm_batch *b, int *out);
+
+/* Release the batch and its device memory.  NULL-safe. */
+void ssm_batch_destroy(ssm_batch *b);
 
 /* ---- learned initial guess of step 1 (SSM_FP32C_LEARNED, SSM_COEF_COUPLED3D) ----
  * The paper has no counterpart; its step 1 (§2.3, eq. SSTM:scheme 1) only needs

@@ -23,11 +23,13 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "ssm_drift_noalloc", "SSM",
+    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "load_ws",
+    "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
+    "ssm_ws_num_params",
 ]
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
-SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU = 0, 1, 2
+SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU, SSM_COEF_COUPLED1D = 0, 1, 2, 3
 SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
 SSM_STAGE_Y, SSM_STAGE_B = 0, 1
 
@@ -100,7 +102,92 @@ _SIGS = {
     "ssm_ws_train": (_i32, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _i64, _i32, _i32,
                             ctypes.c_float, _u64, _vp, _sz, _DP]),
     "ssm_ws_params": (_i32, [_vp, _sz, ctypes.POINTER(ctypes.c_float)]),
+    "ssm_batch_create": (_i32, [_i32, _vp, ctypes.POINTER(ssm_opts), ctypes.POINTER(_vp)]),
+    "ssm_batch_run_steps": (_i32, [_vp, _i64]),
+    "ssm_batch_run": (_i32, [_vp]),
+    "ssm_batch_sync": (_i32, [_vp]),
+    "ssm_batch_get_state": (_i32, [_vp, _i32, _DP, ctypes.POINTER(_i64)]),
+    "ssm_batch_moments": (_i32, [_vp, _i32, _DP]),
+    "ssm_batch_stats": (_i32, [_vp, ctypes.POINTER(ssm_stats_t)]),
+    "ssm_batch_autotune": (_i32, [_vp, _DP]),
+    "ssm_batch_get_plan": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "ssm_batch_destroy": (None, [_vp]),
 }
+
+
+class ssm_ens_desc(ctypes.Structure):
+    _fields_ = [("d", _i32), ("N", _i64), ("h", _dbl), ("T", _dbl), ("seed", _u64), ("fine_log2", _i32)]
+
+
+class Batch:
+    """Many independent ensembles (coupled coefficient set at d = 1 or 3) advanced by
+    one graph launch.  ``descs``: iterable of dicts with keys d, N, h, T, seed and
+    optionally fine_log2."""
+
+    def __init__(self, descs, stream=None, **opt):
+        descs = list(descs)
+        arr = (ssm_ens_desc * len(descs))()
+        for k, dsc in enumerate(descs):
+            arr[k].d, arr[k].N, arr[k].h, arr[k].T = int(dsc["d"]), int(dsc["N"]), float(dsc["h"]), float(dsc["T"])
+            arr[k].seed, arr[k].fine_log2 = int(dsc["seed"]), int(dsc.get("fine_log2", 0))
+        self.descs = descs
+        self.opts = ssm_opts_default(**opt)
+        if stream is not None:
+            self._stream = stream
+            self.opts.stream = int(stream.cuda_stream) or None
+        out = _vp()
+        _check(lib().ssm_batch_create(len(descs), ctypes.cast(arr, _vp), ctypes.byref(self.opts), ctypes.byref(out)),
+               "ssm_batch_create")
+        self.b = out
+
+    def run(self):
+        _check(lib().ssm_batch_run(self.b), "ssm_batch_run")
+
+    def run_steps(self, k):
+        _check(lib().ssm_batch_run_steps(self.b, int(k)), "ssm_batch_run_steps")
+
+    def sync(self):
+        _check(lib().ssm_batch_sync(self.b), "ssm_batch_sync")
+
+    def get_state(self, e):
+        dsc = self.descs[e]
+        x = np.empty((int(dsc["N"]), int(dsc["d"])))
+        n = _i64(0)
+        _check(lib().ssm_batch_get_state(self.b, int(e), _dp(x), ctypes.byref(n)), "ssm_batch_get_state")
+        return x, int(n.value)
+
+    def moments(self, e):
+        out = np.empty((4, int(self.descs[e]["d"])))
+        _check(lib().ssm_batch_moments(self.b, int(e), _dp(out)), "ssm_batch_moments")
+        return out
+
+    def stats(self):
+        s = ssm_stats_t()
+        _check(lib().ssm_batch_stats(self.b, ctypes.byref(s)), "ssm_batch_stats")
+        return {"ensemble_steps": s.steps, "newton_passes": s.newton_passes, "newton_rows": s.newton_rows,
+                "drift_rows": s.drift_rows, "batch_steps": s.max_passes}
+
+    def autotune(self):
+        best = _dbl(0.0)
+        _check(lib().ssm_batch_autotune(self.b, ctypes.byref(best)), "ssm_batch_autotune")
+        return float(best.value)
+
+    def plan(self):
+        out = (_i32 * 5)()
+        _check(lib().ssm_batch_get_plan(self.b, out), "ssm_batch_get_plan")
+        return dict(zip(("packed", "threads", "targets_per_thread_d1", "targets_per_thread_d3", "chunk_len"),
+                        list(out)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().ssm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 _FP = ctypes.POINTER(ctypes.c_float)
 

@@ -15,7 +15,6 @@
 namespace ssm {
 cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
                       const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st);
-bool pair_shape_supported(int threads, int rpt);
 int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt);
 int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out);
 cudaError_t launch_init_x0(ssm_ctx *c);
@@ -64,7 +63,12 @@ int chunks_cap(int64_t N, int nc) {
     return cap < 1 ? 1 : (int)cap;
 }
 
-int kind_nc(int kind) { return kind == PK_NEWTON3 ? 4 : (kind == PK_DRIFT3 ? 3 : 1); }
+int kind_nc(int kind) {
+    return kind == PK_NEWTON3 ? 4 : kind == PK_DRIFT3 ? 3 : kind == PK_NEWTON1 ? 2 : 1;
+}
+bool is_coupled(int coef) { return coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D; }
+int newton_kind(int d) { return d == 1 ? PK_NEWTON1 : PK_NEWTON3; }
+int drift_kind(int coef) { return (coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM_COEF_COUPLED1D) ? PK_DRIFT1 : PK_DRIFT3; }
 
 // Resident-block slots of the device for a pair kernel shape (0 = no device).
 int device_slots(int kind, bool fp32, bool vec2, int threads, int rpt) {
@@ -138,9 +142,10 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.y = take(sizeof(double) * d * Np);
     L.stage = take(sizeof(double) * d * Np);
     size_t part = 0;
-    if (coef == SSM_COEF_COUPLED3D) {
-        part = (size_t)chunks_cap(N, 4) * 4;
-        if ((size_t)chunks_cap(N, 3) * 3 > part) part = (size_t)chunks_cap(N, 3) * 3;
+    if (is_coupled(coef)) {
+        const int nn = d + 1, nd = d;   // step-1 and drift partial-sum components
+        part = (size_t)chunks_cap(N, nn) * nn;
+        if ((size_t)chunks_cap(N, nd) * nd > part) part = (size_t)chunks_cap(N, nd) * nd;
     } else if (coef == SSM_COEF_CUBIC1D_GAUSS) {
         part = (size_t)chunks_cap(N, 1);
     }
@@ -148,7 +153,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.mpart = take(sizeof(double) * RED_BLOCKS * 12);
     L.mom = take(sizeof(double) * 12);
     L.ymean = take(sizeof(double) * 4);
-    const bool nt = coef == SSM_COEF_COUPLED3D;
+    const bool nt = is_coupled(coef);
     L.act0 = take(nt ? sizeof(int) * Np : 0);
     L.act1 = take(nt ? sizeof(int) * Np : 0);
     L.cnt = take(sizeof(int) * (kmax + 2));
@@ -184,8 +189,8 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
     if (coef == SSM_COEF_CUBIC1D_GAUSS) {
         if (d != 1) return SSM_EINVAL;
         Lv = 1.0;
-    } else if (coef == SSM_COEF_COUPLED3D) {
-        if (d != 3) return SSM_EINVAL;
+    } else if (coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D) {
+        if (d != (coef == SSM_COEF_COUPLED3D ? 3 : 1)) return SSM_EINVAL;
         Lv = 1.0 / 16.0;
     } else if (coef == SSM_COEF_OU) {
         if (d < 1 || d > 3) return SSM_EINVAL;
@@ -248,20 +253,20 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if ((e = launch_ou_implicit(c)) != cudaSuccess) return e;
         return launch_euler(c, 0.0);
     }
-    // SSM_COEF_COUPLED3D
+    // SSM_COEF_COUPLED3D / SSM_COEF_COUPLED1D
     if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
     if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
         if ((e = ws_forward_start(c)) != cudaSuccess) return e;
     int *a_in = c->act0, *a_out = c->act1;
     for (int k = 0; k < c->kmax; ++k) {
-        if ((e = pair_sums(PK_NEWTON3, f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0, c->part,
+        if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0, c->part,
                            c->st)) != cudaSuccess)
             return e;
         if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
         int *t = a_in; a_in = a_out; a_out = t;
     }
     if ((e = launch_step_stats(c)) != cudaSuccess) return e;
-    if ((e = pair_sums(PK_DRIFT3, f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale, c->part,
+    if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale, c->part,
                        c->st)) != cudaSuccess)
         return e;
     return launch_euler(c, bscale);
@@ -302,8 +307,8 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->kmax = o.newton_kmax;
     c->tol = o.newton_tol > 0.0 ? o.newton_tol : (o.precision == SSM_FP64 ? 1e-13 : 1e-10);
     const bool f32 = o.precision != SSM_FP64;
-    c->plan_newton = make_plan(N, f32, PK_NEWTON3, o.tile_chunks);
-    c->plan_drift = make_plan(N, f32, coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, o.tile_chunks);
+    c->plan_newton = make_plan(N, f32, newton_kind(d), o.tile_chunks);
+    c->plan_drift = make_plan(N, f32, drift_kind(coef), o.tile_chunks);
     Layout L = make_layout(d, N, coef, c->kmax);
 
     cudaError_t e = cudaSuccess;
@@ -528,15 +533,16 @@ ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream
 ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
     if (!c || (which != 0 && which != 1)) return SSM_EINVAL;
     if (c->status != SSM_OK) return (ssm_status)c->status;
-    if (c->coef == SSM_COEF_OU || (which == 0 && c->coef != SSM_COEF_COUPLED3D)) return SSM_EINVAL;
+    if (c->coef == SSM_COEF_OU || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
     cudaError_t e;
     if (which == 0) {
-        e = pair_sums(PK_NEWTON3, f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0, c->part, c->st);
+        e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0, c->part,
+                      c->st);
     } else {
         double scale, bscale;
         drift_scale(c->coef, f32, c->N, &scale, &bscale);
-        e = pair_sums(c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3, f32, c->plan_drift, c->y, c->y,
+        e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y,
                       nullptr, nullptr, c->N, c->Np, scale, c->part, c->st);
     }
     if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
@@ -553,19 +559,19 @@ ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
     const bool f32 = fp32_pairs(c);
     double scale, bscale;
     drift_scale(c->coef, f32, c->N, &scale, &bscale);
-    const int kd = c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3;
-    const int kinds[2] = { PK_NEWTON3, kd };
+    const int kd = drift_kind(c->coef), kn = newton_kind(c->d);
+    const int kinds[2] = { kn, kd };
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SSM_ECUDA;
     cudaError_t err = cudaSuccess;
     for (int q = 0; q < 2 && err == cudaSuccess; ++q) {
         const int kind = kinds[q];
-        if (kind == PK_NEWTON3 && c->coef != SSM_COEF_COUPLED3D) continue;
-        const double *src = kind == PK_NEWTON3 ? c->x : c->y;
-        const double sc = kind == PK_NEWTON3 ? 1.0 : scale;
+        if (q == 0 && !is_coupled(c->coef)) continue;
+        const double *src = q == 0 ? c->x : c->y;
+        const double sc = q == 0 ? 1.0 : scale;
         int cand[32][3];
         const int nc = pair_shape_candidates(kind, f32, cand, 32);
-        Plan best = kind == PK_NEWTON3 ? c->plan_newton : c->plan_drift;
+        Plan best = q == 0 ? c->plan_newton : c->plan_drift;
         float best_t = 1e30f;
         for (int k = 0; k < nc && err == cudaSuccess; ++k) {
             const int slots = device_slots(kind, f32, cand[k][0] != 0, cand[k][1], cand[k][2]);
@@ -581,7 +587,7 @@ ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
             if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
             if (err == cudaSuccess && ms < best_t) { best_t = ms; best = p; }
         }
-        if (kind == PK_NEWTON3) c->plan_newton = best; else c->plan_drift = best;
+        if (q == 0) c->plan_newton = best; else c->plan_drift = best;
         if (best_ms) best_ms[q] = best_t / 2.0;
     }
     cudaEventDestroy(e0);
@@ -600,9 +606,9 @@ ssm_status ssm_get_plan(ssm_ctx *c, int which, int *out) {
 
 ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
     if (!c || !in || (which != 0 && which != 1)) return SSM_EINVAL;
-    if (c->coef == SSM_COEF_OU || (which == 0 && c->coef != SSM_COEF_COUPLED3D)) return SSM_EINVAL;
+    if (c->coef == SSM_COEF_OU || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
-    const int kind = which == 0 ? PK_NEWTON3 : (c->coef == SSM_COEF_CUBIC1D_GAUSS ? PK_DRIFT1 : PK_DRIFT3);
+    const int kind = which == 0 ? newton_kind(c->d) : drift_kind(c->coef);
     int cand[32][3];
     const int nc = pair_shape_candidates(kind, f32, cand, 32);
     bool ok = false;

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "particle_ops.cuh"
 #include "ssm_device.cuh"
 
 namespace ssm {
@@ -68,15 +69,6 @@ __device__ __forceinline__ void moments_epilogue(double (&m)[4 * D], int64_t N, 
             if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
         }
     }
-}
-
-template <int D>
-__device__ __forceinline__ void add_powers(double (&m)[4 * D], int c, double v) {
-    const double v2 = v * v;
-    m[0 * D + c] += v;
-    m[1 * D + c] += v2;
-    m[2 * D + c] += v2 * v;
-    m[3 * D + c] += v2 * v2;
 }
 
 // X_0^i = mean + std Z^i, Z from Philox stream 0 at step 0 (and its moments).
@@ -166,31 +158,26 @@ k_ou_implicit(const double *x, double *y, int64_t N, int64_t Np, double inv, dou
 }
 
 // ---------------------------------------------------------------------------
-// Step 1, SSM_COEF_COUPLED3D.  The implicit equation
+// Step 1 of the coupled sets (d = 3 and d = 1).  The implicit equation
 //   F(Y) = Y - X - h ( -Y|Y|^2 + 0.5 S(Y) ) = 0,  S(Y) = (1/N) sum_j (X_j - Y) w_j,
 //   w_j = 1 / (1 + |X_j - Y|^2)
 // is solved for all particles at once in passes.  Each pass evaluates S and
 // Sw = (1/N) sum_j w_j at the current Y of every unconverged particle (the
-// O(N^2) pair kernel), then this kernel forms the residual in double; a
-// particle whose max-norm residual is within tol is done.  Otherwise Y moves to
-// the root of the local model
-//   u = X + h ( -u|u|^2 + 0.5 ( S - Sw (u - Y) ) ),
-// whose cubic part is exact and whose pair part is S linearised with the
-// diagonal -Sw I of its Jacobian (1/N) sum_j (-w_j I + 2 w_j^2 d_j d_j^T).  That
-// local problem has the Jacobian a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw), which
-// Sherman-Morrison inverts in closed form; a few Newton steps solve it to
-// rounding.  The outer iteration contracts by about 0.5 h |(2 w^2 d d^T)| per pass.
+// O(N^2) pair kernel), then k_newton_update forms the FP64 residual and either
+// retires the particle or moves it (newton_update_particle).  The outer
+// iteration contracts by about 0.5 h |(2 w^2 d d^T)| per pass.
 // ---------------------------------------------------------------------------
 // Plain start Y = X (a learned start, when enabled, overwrites Y afterwards);
 // resets the active list, pass counters and histogram, and keeps the moments of
 // X_n that the learned start and the training-data collection use.
+template <int D>
 __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
                                int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
                                const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) y[c * Np + i] = x[c * Np + i];
+        for (int c = 0; c < D; ++c) y[c * Np + i] = x[c * Np + i];
         act[i] = (int)i;
         passes[i] = 0;
     }
@@ -198,16 +185,18 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
         cnt[0] = (int)N;
         for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
         for (int k = 0; k < 16; ++k) hist[k] = 0;
-        for (int k = 0; k < 12; ++k) mom_prev[k] = mom[k];
+        for (int k = 0; k < 4 * D; ++k) mom_prev[k] = mom[k];
     }
 }
 
+template <int D>
 __global__ void __launch_bounds__(256)
 k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int *__restrict__ act_in,
                 const int *__restrict__ cnt_in, int *__restrict__ act_out, int *__restrict__ cnt_out,
                 const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h, double tol,
                 int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err,
                 double *__restrict__ sconv, int restart_pass, long long *counters) {
+    constexpr int NC = D + 1;
     __shared__ int bh[16];
     __shared__ int nrestart;
     if (threadIdx.x < 16) bh[threadIdx.x] = 0;
@@ -219,75 +208,38 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
     int i = 0;
     if (t < n_in) {
         i = act_in[t];
-        double S[3] = { 0.0, 0.0, 0.0 }, Sw = 0.0;
+        double S[D], Sw = 0.0, Y[D], X[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) S[c] = 0.0;
         for (int k = 0; k < chunks; ++k) {
-            const double *pk = part + (int64_t)k * 4 * Np + t;
-            S[0] += pk[0];
-            S[1] += pk[Np];
-            S[2] += pk[2 * Np];
-            Sw += pk[3 * Np];
+            const double *pk = part + (int64_t)k * NC * Np + t;
+#pragma unroll
+            for (int c = 0; c < D; ++c) S[c] += pk[c * Np];
+            Sw += pk[D * Np];
         }
         const double invN = 1.0 / (double)N;
-        double Y[3], X[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < D; ++c) {
             S[c] *= invN;
             Y[c] = y[c * Np + i];
             X[c] = x[c * Np + i];
         }
         Sw *= invN;
-        if (fp32_targets) {
-            // The pair kernel evaluated the numerators at the FP32 rounding of Y;
-            // (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y)) corrects them exactly.
-#pragma unroll
-            for (int c = 0; c < 3; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
-        }
-        const double yy = Y[0] * Y[0] + Y[1] * Y[1] + Y[2] * Y[2];
-        double rinf = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
-            rinf = fmax(rinf, fabs(r));
-            if (r != r) rinf = r;   // NaN propagates as "not converged"
-        }
-        if (rinf <= tol) {
+        const int r = newton_update_particle<D>(S, Sw, Y, X, h, tol, fp32_targets != 0, pass, kmax, restart_pass);
+        if (r == UPD_CONVERGED) {
             passes[i] = pass + 1;
             atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sconv[c * Np + i] = S[c];
-        } else if (pass + 1 >= kmax || !(rinf == rinf && fabs(Y[0]) + fabs(Y[1]) + fabs(Y[2]) < 1e300)) {
+            for (int c = 0; c < D; ++c) sconv[c * Np + i] = S[c];
+        } else if (r == UPD_NOCONV || r == UPD_NONFINITE) {
             passes[i] = pass + 1;
-            atomicOr(err, rinf == rinf ? ERR_NOCONV : ERR_NONFINITE);
-        } else if (pass + 1 == restart_pass) {
-            // A learned start that has not converged after restart_pass passes:
-            // fall back to the plain start Y = X and continue with plain passes.
-#pragma unroll
-            for (int c = 0; c < 3; ++c) y[c * Np + i] = X[c];
-            atomicAdd(&nrestart, 1);
-            keep = true;
+            atomicOr(err, r == UPD_NOCONV ? ERR_NOCONV : ERR_NONFINITE);
         } else {
-            double u[3] = { Y[0], Y[1], Y[2] };
-            for (int it = 0; it < 30; ++it) {
-                const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                double g[3];
+            // UPD_RESTART (a learned start that missed the tolerance after
+            // restart_pass passes goes back to the plain start Y = X) or UPD_CONTINUE
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * (u[c] - Y[c]);
-                const double a = 1.0 + h * uu + 0.5 * h * Sw;
-                const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
-                const double f = 2.0 * h * ug / (a + 2.0 * h * uu);
-                double smax = 0.0, umax = 1.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double s = (g[c] - f * u[c]) / a;
-                    u[c] -= s;
-                    smax = fmax(smax, fabs(s));
-                    umax = fmax(umax, fabs(u[c]));
-                }
-                if (smax <= 1e-16 * umax) break;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) y[c * Np + i] = u[c];
+            for (int c = 0; c < D; ++c) y[c * Np + i] = Y[c];
+            if (r == UPD_RESTART) atomicAdd(&nrestart, 1);
             keep = true;
         }
     }
@@ -349,28 +301,10 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
                 b[c] = s * bscale;
             }
         }
-        if (fine_r <= 1) {
-            double z[3];
-            normals<D>(seed, (uint32_t)i, (uint32_t)n, 1u, z);
-#pragma unroll
-            for (int c = 0; c < D; ++c) dw[c] = sqrt_h * z[c];
-        } else {
-#pragma unroll
-            for (int c = 0; c < D; ++c) dw[c] = 0.0;
-            for (int r = 0; r < fine_r; ++r) {
-                double z[3];
-                normals<D>(seed, (uint32_t)i, (uint32_t)(n * fine_r + r), 1u, z);
-#pragma unroll
-                for (int c = 0; c < D; ++c) dw[c] += sqrt_hf * z[c];
-            }
-        }
+        brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            double sig;
-            if (coef == SSM_COEF_CUBIC1D_GAUSS) sig = 0.4 * yv[c] + 0.1;
-            else if (coef == SSM_COEF_COUPLED3D) sig = 0.3 * yv[c] + 0.2;
-            else sig = eta;
-            const double xn = yv[c] + h * b[c] + sig * dw[c];
+            const double xn = yv[c] + h * b[c] + sigma_of(coef, yv[c], eta) * dw[c];
             x[c * Np + i] = xn;
             add_powers<D>(m, c, xn);
         }
@@ -462,6 +396,14 @@ cudaError_t launch_init_x0(ssm_ctx *c) {
     return cudaGetLastError();
 }
 
+// X_0 and its moments for arrays outside a context (used by the batched form).
+cudaError_t launch_init_x0_raw(int d, double *x, int64_t N, int64_t Np, uint64_t seed, double mean, double sd,
+                               double *mpart, unsigned *ticket, double *mom, int *err, cudaStream_t st) {
+    if (d == 1) k_init_x0<1><<<RED_BLOCKS, EUL_THREADS, 0, st>>>(x, N, Np, seed, mean, sd, mpart, ticket, mom, err);
+    else k_init_x0<3><<<RED_BLOCKS, EUL_THREADS, 0, st>>>(x, N, Np, seed, mean, sd, mpart, ticket, mom, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(ssm_ctx *c) {
     if (c->d == 1) k_moments<1><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->mpart, c->ticket, c->mom, c->err);
     else if (c->d == 2) k_moments<2><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->N, c->Np, c->mpart, c->ticket, c->mom, c->err);
@@ -483,17 +425,23 @@ cudaError_t launch_ou_implicit(ssm_ctx *c) {
 }
 
 cudaError_t launch_newton_begin(ssm_ctx *c) {
-    k_newton_begin<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
-                                                       c->mom, c->mom_prev, c->N, c->Np);
+    if (c->d == 1)
+        k_newton_begin<1><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
+                                                              c->mom, c->mom_prev, c->N, c->Np);
+    else
+        k_newton_begin<3><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
+                                                              c->mom, c->mom_prev, c->N, c->Np);
     return cudaGetLastError();
 }
 
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32) {
-    k_newton_update<<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, c->cnt + pass + 1,
-                                                        c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32,
-                                                        pass, c->kmax, c->passes, c->hist, c->err, c->sconv,
-                                                        (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1,
-                                                        c->counters);
+    const int rp = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1;
+#define SSM_UPD(D) k_newton_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, \
+        c->cnt + pass + 1, c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->passes, \
+        c->hist, c->err, c->sconv, rp, c->counters)
+    if (c->d == 1) SSM_UPD(1);
+    else SSM_UPD(3);
+#undef SSM_UPD
     return cudaGetLastError();
 }
 

@@ -1,0 +1,119 @@
+// particle_ops.cuh -- per-particle device code of the SSM step shared by the
+// single-context kernels (k_particle.cu) and the batched kernels (batch.cu).
+// References: Chen & dos Reis, arXiv:2105.09688, §2.3 (eq. SSTM:scheme 1 and 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssm_device.cuh"
+
+namespace ssm {
+
+// Outcome of one update of step 1 for a particle.
+enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 3, UPD_NONFINITE = 4 };
+
+// Step 1 of the coupled set, v(y, mu) = -y|y|^2 + 0.5 S(y), for one particle after
+// a pair pass: S[D] = (1/N) sum_j (X_j - fl(Y)) w_j and Sw = (1/N) sum_j w_j were
+// evaluated at the current Y (fl = FP32 rounding when fp32_targets, exact
+// otherwise).  Forms the FP64 residual r = Y - X - h v(Y); if max|r| <= tol the
+// particle is done (S is returned in S_conv).  Otherwise Y moves to the root of
+// the local model u = X + h(-u|u|^2 + 0.5(S - Sw (u - Y))): the cubic part exact,
+// the pair part linearised with the diagonal -Sw I of its Jacobian.  The local
+// Jacobian a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw) is inverted by
+// Sherman-Morrison; Newton on the local model converges to rounding in a few steps.
+template <int D>
+__device__ __forceinline__ int newton_update_particle(double *S, double Sw, double *Y, const double *X, double h,
+                                                      double tol, bool fp32_targets, int pass, int kmax,
+                                                      int restart_pass) {
+    if (fp32_targets)   // numerators were taken at fl(Y): (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y))
+#pragma unroll
+        for (int c = 0; c < D; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
+    double yy = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) yy += Y[c] * Y[c];
+    double rinf = 0.0;
+    bool bad = !(yy < 1e300);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
+        if (!(r == r)) bad = true;
+        rinf = fmax(rinf, fabs(r));
+    }
+    if (bad) return UPD_NONFINITE;
+    if (rinf <= tol) return UPD_CONVERGED;
+    if (pass + 1 >= kmax) return UPD_NOCONV;
+    if (pass + 1 == restart_pass) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) Y[c] = X[c];
+        return UPD_RESTART;
+    }
+    double u[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) u[c] = Y[c];
+    for (int it = 0; it < 30; ++it) {
+        double uu = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) uu += u[c] * u[c];
+        double g[D], ug = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * (u[c] - Y[c]);
+            ug += u[c] * g[c];
+        }
+        const double a = 1.0 + h * uu + 0.5 * h * Sw;
+        const double f = 2.0 * h * ug / (a + 2.0 * h * uu);
+        double smax = 0.0, umax = 1.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double s = (g[c] - f * u[c]) / a;
+            u[c] -= s;
+            smax = fmax(smax, fabs(s));
+            umax = fmax(umax, fabs(u[c]));
+        }
+        if (smax <= 1e-16 * umax) break;
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) Y[c] = u[c];
+    return UPD_CONTINUE;
+}
+
+// Brownian increment dW_n^i on the step's own grid (fine_r <= 1) or as the sum of
+// fine_r increments of the finer grid (runs at different h share one path).
+template <int D>
+__device__ __forceinline__ void brownian(uint64_t seed, int64_t i, long long n, double sqrt_h, int fine_r,
+                                         double sqrt_hf, double *dw) {
+    if (fine_r <= 1) {
+        double z[3];
+        normals<D>(seed, (uint32_t)i, (uint32_t)n, 1u, z);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dw[c] = sqrt_h * z[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dw[c] = 0.0;
+        for (int r = 0; r < fine_r; ++r) {
+            double z[3];
+            normals<D>(seed, (uint32_t)i, (uint32_t)(n * fine_r + r), 1u, z);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dw[c] += sqrt_hf * z[c];
+        }
+    }
+}
+
+// Diffusion coefficient of each coefficient set, evaluated at Y (step 2).
+__device__ __forceinline__ double sigma_of(int coef, double y, double eta) {
+    if (coef == SSM_COEF_CUBIC1D_GAUSS) return 0.4 * y + 0.1;
+    if (coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D) return 0.3 * y + 0.2;
+    return eta;
+}
+
+template <int D>
+__device__ __forceinline__ void add_powers(double (&m)[4 * D], int c, double v) {
+    const double v2 = v * v;
+    m[0 * D + c] += v;
+    m[1 * D + c] += v2;
+    m[2 * D + c] += v2 * v;
+    m[3 * D + c] += v2 * v2;
+}
+
+}  // namespace ssm

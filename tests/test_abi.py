@@ -77,3 +77,22 @@ def test_learned_form_needs_coupled_set(S):
     o = S.ssm_opts_default(precision=S.SSM_FP32C_LEARNED)
     with pytest.raises(S.SSMError):
         S.ssm_create(1, 10, 0.01, 1.0, S.SSM_COEF_CUBIC1D_GAUSS, 0, o)
+
+
+@pytest.mark.parametrize("desc", [
+    dict(d=2, N=100, h=0.1, T=1.0, seed=0),        # d must be 1 or 3
+    dict(d=3, N=0, h=0.1, T=1.0, seed=0),          # empty ensemble
+    dict(d=3, N=100, h=0.95, T=1.9, seed=0),       # h above 1/(1 + 2/16) (Theorem 2.3)
+    dict(d=1, N=100, h=0.3, T=1.0, seed=0),        # T/h not an integer
+    dict(d=1, N=100, h=2.0 ** -4, T=1.0, seed=0, fine_log2=3),   # fine grid coarser than h
+])
+def test_batch_rejects_bad_descriptors_before_touching_the_gpu(S, desc):
+    good = dict(d=1, N=10, h=0.25, T=1.0, seed=1)
+    with pytest.raises(S.SSMError) as e:
+        S.Batch([good, desc])
+    assert e.value.status == S.SSM_EINVAL
+
+
+def test_batch_rejects_unsupported_precision(S):
+    with pytest.raises(S.SSMError):
+        S.Batch([dict(d=1, N=10, h=0.25, T=1.0, seed=1)], precision=S.SSM_FP32C_LEARNED)
