@@ -77,7 +77,10 @@ typedef enum { SSM_FP64 = 0, SSM_FP32C = 1, SSM_FP32C_LEARNED = 2 } ssm_precisio
 typedef struct {
     int precision;          /* ssm_precision; default SSM_FP64 */
     double newton_tol;      /* step 1 stops when max_c |r_c| <= newton_tol, with
-                               r = Y - X - h v(Y, mu^X); default 1e-13 (FP64), 1e-10 (FP32C) */
+                               r = Y - X - h v(Y, mu^X); 0 = default: 1e-13 (FP64);
+                               FP32 forms: max(1e-10, 2^-27 h (1 + 8/sqrt(N))), i.e. 1e-10
+                               at h <= 2^-8, N >= 2^10, and the FP32 evaluation floor of
+                               the residual at larger h or small N */
     int newton_kmax;        /* maximum N-body passes of one implicit step; default 12 */
     int fine_log2;          /* 0: dW on the step's own grid.  L > 0: the Brownian path
                                lives on the grid T 2^-L (h must be a multiple of it) and

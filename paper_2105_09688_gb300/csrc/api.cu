@@ -47,7 +47,10 @@ bool fp32_pairs(const ssm_ctx *c) { return c->prec != SSM_FP64; }
 void drift_scale(int coef, bool fp32, int64_t N, double *scale, double *bscale) {
     const double cexp = coef == SSM_COEF_CUBIC1D_GAUSS ? 1.0 : 0.5;   // exp(-cexp r^2)
     const double cb = coef == SSM_COEF_CUBIC1D_GAUSS ? 0.5 : 1.0;     // coefficient of the integral
-    *scale = fp32 ? sqrt(cexp * LOG2E) : 1.0;
+    // FP32: exp(-c r^2) = 2^(-|s r|^2) with s = sqrt(c log2 e).  FP64: the d = 1
+    // kernel evaluates exp(-r^2), so s = sqrt(c); the d = 3 kernel has c = 1/2 built in.
+    const bool d1 = coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM_COEF_COUPLED1D;
+    *scale = fp32 ? sqrt(cexp * LOG2E) : (d1 ? sqrt(cexp) : 1.0);
     *bscale = cb / ((double)N * *scale);
 }
 
@@ -126,7 +129,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -166,6 +169,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.wsw = take(nt ? 65536 * sizeof(float) : 0);
     L.sconv = take(nt ? sizeof(double) * 3 * Np : 0);
     L.mom_prev = take(sizeof(double) * 12);
+    L.rprev = take(nt ? sizeof(float) * Np : 0);
     L.total = o;
     return L;
 }
@@ -305,7 +309,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->M = (int64_t)nearbyint(T / h);
     c->n = 0;
     c->kmax = o.newton_kmax;
-    c->tol = o.newton_tol > 0.0 ? o.newton_tol : (o.precision == SSM_FP64 ? 1e-13 : 1e-10);
+    c->tol = o.newton_tol > 0.0 ? o.newton_tol : default_tol(o.precision != SSM_FP64, h, N);
     const bool f32 = o.precision != SSM_FP64;
     c->plan_newton = make_plan(N, f32, newton_kind(d), o.tile_chunks);
     c->plan_drift = make_plan(N, f32, drift_kind(coef), o.tile_chunks);
@@ -349,6 +353,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->ws_w = (float *)(b + L.wsw);
     c->sconv = (double *)(b + L.sconv);
     c->mom_prev = (double *)(b + L.mom_prev);
+    c->rprev = (float *)(b + L.rprev);
     c->ws_loaded = 0;
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0

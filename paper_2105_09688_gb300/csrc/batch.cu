@@ -50,9 +50,10 @@ struct BEns {                // one ensemble, in device memory
     int64_t N, Np, M, chunk_len, seg0, nseg;
     long long n;
     uint64_t seed;
-    double h, sqrt_h, sqrt_hf, scale, bscale;
+    double h, sqrt_h, sqrt_hf, scale, bscale, tol;
     double *x, *y, *part, *mom;
     int *act0, *act1, *cnt;
+    float *rprev;
 };
 
 struct BGlobal {             // batch-wide device state
@@ -187,7 +188,7 @@ kb_pair(BEns *ens, int n_ens, const BGlobal *g) {
 }
 
 template <int D>
-__device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, int i, double tol, bool fp32, int kmax) {
+__device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, int i, bool fp32, int kmax) {
     constexpr int NC = D + 1;
     double S[D], Sw = 0.0, Y[D], X[D];
 #pragma unroll
@@ -206,7 +207,7 @@ __device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, in
         X[c] = E.x[c * E.Np + i];
     }
     Sw *= invN;
-    const int r = newton_update_particle<D>(S, Sw, Y, X, E.h, tol, fp32, pass, kmax, -1);
+    const int r = newton_update_particle<D>(S, Sw, Y, X, E.h, E.tol, fp32, pass, kmax, -1, &E.rprev[i]);
     if (r == UPD_CONTINUE)
 #pragma unroll
         for (int c = 0; c < D; ++c) E.y[c * E.Np + i] = Y[c];
@@ -216,7 +217,7 @@ __device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, in
 // Step-1 updates of every active target; the last block advances the pass and
 // decides whether the pass loop runs again.
 __global__ void __launch_bounds__(SEGT)
-kb_update(BEns *ens, int n_ens, BGlobal *g, double tol, int kmax, int fp32, cudaGraphConditionalHandle hpass) {
+kb_update(BEns *ens, int n_ens, BGlobal *g, int kmax, int fp32, cudaGraphConditionalHandle hpass) {
     __shared__ long long pref[MAX_ENS + 1];
     const int pass = g->pass;
     block_prefix(pref, n_ens, [&](int e) -> long long { return ens[e].active ? ens[e].cnt[pass] : 0; });
@@ -231,8 +232,8 @@ kb_update(BEns *ens, int n_ens, BGlobal *g, double tol, int kmax, int fp32, cuda
             const BEns &E = ens[e];
             const int64_t t = idx - pref[e];
             i = ((pass & 1) ? E.act1 : E.act0)[t];
-            const int r = E.d == 1 ? update_one<1>(E, pass, t, i, tol, fp32 != 0, kmax)
-                                   : update_one<3>(E, pass, t, i, tol, fp32 != 0, kmax);
+            const int r = E.d == 1 ? update_one<1>(E, pass, t, i, fp32 != 0, kmax)
+                                   : update_one<3>(E, pass, t, i, fp32 != 0, kmax);
             if (r == UPD_CONTINUE) keep = true;
             else if (r == UPD_NOCONV) atomicOr(&g->err, ERR_NOCONV);
             else if (r == UPD_NONFINITE) atomicOr(&g->err, ERR_NONFINITE);
@@ -449,7 +450,6 @@ cudaError_t build_graph(ssm_batch *b) {
     int n = b->n;
     BGlobal *gl = b->d_g;
     int kmax = b->kmax;
-    double tol = b->tol;
     int fp32 = b->f32 ? 1 : 0;
     long long *segp = b->d_seg_pref;
     double *mseg = b->d_mseg;
@@ -469,7 +469,7 @@ cudaError_t build_graph(ssm_batch *b) {
         cudaGraphNode_t np, nu;
         void *a_pair[] = { &ens, &n, &glc };
         e = kernel_node(pbody, &np, nullptr, 0, pair_kernel<true>(b->f32, b->shape), b->grid_pair[0], BT, a_pair);
-        void *a_upd[] = { &ens, &n, &gl, &tol, &kmax, &fp32, &hpass };
+        void *a_upd[] = { &ens, &n, &gl, &kmax, &fp32, &hpass };
         if (e == cudaSuccess) e = kernel_node(pbody, &nu, &np, 1, (void *)kb_update, b->grid_small, SEGT, a_upd);
     }
     void *a_drift[] = { &ens, &n, &glc };
@@ -558,7 +558,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
     std::vector<int64_t> off(n);
     size_t o8 = 0;
     auto take = [&](size_t bytes) { size_t at = o8; o8 = (o8 + bytes + 255) & ~(size_t)255; return at; };
-    struct Offs { size_t x, y, part, mom, a0, a1, cnt; };
+    struct Offs { size_t x, y, part, mom, a0, a1, cnt, rp; };
     std::vector<Offs> of(n);
     long long nseg_total = 0;
     for (int k = 0; k < n; ++k) {
@@ -571,6 +571,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         of[k].mom = take(sizeof(double) * 12);
         of[k].a0 = take(sizeof(int) * Np);
         of[k].a1 = take(sizeof(int) * Np);
+        of[k].rp = take(sizeof(float) * Np);
         of[k].cnt = take(sizeof(int) * (b->kmax + 2));
         nseg_total += (D.N + SEGT - 1) / SEGT;
     }
@@ -592,6 +593,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         E.active = 1;
         E.seed = D.seed;
         E.h = D.h;
+        E.tol = o.newton_tol > 0.0 ? o.newton_tol : default_tol(b->f32, D.h, D.N);
         E.sqrt_h = sqrt(D.h);
         E.fine_r = 1;
         E.sqrt_hf = 0.0;
@@ -600,7 +602,9 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
             E.fine_r = (int)llround(D.h / hf);
             E.sqrt_hf = sqrt(hf);
         }
-        E.scale = b->f32 ? sqrt(0.5 * LOG2E) : 1.0;   // exp(-r^2 / 2) = 2^(-|scale r|^2)
+        // exp(-r^2 / 2) = 2^(-|scale r|^2) in FP32; in FP64 the d = 1 kernel
+        // evaluates exp(-r^2) (scale 1/sqrt(2)) and the d = 3 kernel has the 1/2 built in
+        E.scale = b->f32 ? sqrt(0.5 * LOG2E) : (D.d == 1 ? sqrt(0.5) : 1.0);
         E.bscale = 1.0 / ((double)D.N * E.scale);
         E.x = (double *)(b->mem + of[k].x);
         E.y = (double *)(b->mem + of[k].y);
@@ -608,6 +612,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         E.mom = (double *)(b->mem + of[k].mom);
         E.act0 = (int *)(b->mem + of[k].a0);
         E.act1 = (int *)(b->mem + of[k].a1);
+        E.rprev = (float *)(b->mem + of[k].rp);
         E.cnt = (int *)(b->mem + of[k].cnt);
         E.seg0 = segp[k];
         E.nseg = (D.N + SEGT - 1) / SEGT;

@@ -195,7 +195,7 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
                 const int *__restrict__ cnt_in, int *__restrict__ act_out, int *__restrict__ cnt_out,
                 const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h, double tol,
                 int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err,
-                double *__restrict__ sconv, int restart_pass, long long *counters) {
+                double *__restrict__ sconv, int restart_pass, long long *counters, float *__restrict__ rprev) {
     constexpr int NC = D + 1;
     __shared__ int bh[16];
     __shared__ int nrestart;
@@ -225,7 +225,8 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
             X[c] = x[c * Np + i];
         }
         Sw *= invN;
-        const int r = newton_update_particle<D>(S, Sw, Y, X, h, tol, fp32_targets != 0, pass, kmax, restart_pass);
+        const int r = newton_update_particle<D>(S, Sw, Y, X, h, tol, fp32_targets != 0, pass, kmax, restart_pass,
+                                                &rprev[i]);
         if (r == UPD_CONVERGED) {
             passes[i] = pass + 1;
             atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
@@ -438,7 +439,7 @@ cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *a
     const int rp = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1;
 #define SSM_UPD(D) k_newton_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, \
         c->cnt + pass + 1, c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->passes, \
-        c->hist, c->err, c->sconv, rp, c->counters)
+        c->hist, c->err, c->sconv, rp, c->counters, c->rprev)
     if (c->d == 1) SSM_UPD(1);
     else SSM_UPD(3);
 #undef SSM_UPD

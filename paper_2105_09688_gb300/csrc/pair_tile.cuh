@@ -102,7 +102,7 @@ template <> __device__ __forceinline__ void pair<PK_NEWTON1, double>(const doubl
 
 template <typename T> __device__ __forceinline__ T cvt(double v, double scale);
 template <> __device__ __forceinline__ float cvt<float>(double v, double scale) { return (float)(v * scale); }
-template <> __device__ __forceinline__ double cvt<double>(double v, double) { return v; }
+template <> __device__ __forceinline__ double cvt<double>(double v, double scale) { return v * scale; }
 
 // Scalar tile.  src, tgt: FP64 SoA state arrays [D][Np].  Targets t0 + r*THREADS +
 // tid (r < R) below ntgt are particles act[t] (or t without a list).  Block-uniform:

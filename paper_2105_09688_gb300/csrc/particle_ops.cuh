@@ -22,10 +22,17 @@ enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 
 // the pair part linearised with the diagonal -Sw I of its Jacobian.  The local
 // Jacobian a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw) is inverted by
 // Sherman-Morrison; Newton on the local model converges to rounding in a few steps.
+//
+// FP32 pair sums can only certify the residual down to their evaluation floor
+// (rounding of the pair terms and of the FP32 target), which at large h or small
+// N may lie above tol.  A pass normally cuts the residual by ~10^3; when it no
+// longer cuts it tenfold and the residual is within 64 tol, the iteration has
+// reached that floor and the particle is accepted (rprev holds the previous
+// pass's residual of this particle).
 template <int D>
 __device__ __forceinline__ int newton_update_particle(double *S, double Sw, double *Y, const double *X, double h,
                                                       double tol, bool fp32_targets, int pass, int kmax,
-                                                      int restart_pass) {
+                                                      int restart_pass, float *rprev) {
     if (fp32_targets)   // numerators were taken at fl(Y): (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y))
 #pragma unroll
         for (int c = 0; c < D; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
@@ -42,6 +49,8 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
     }
     if (bad) return UPD_NONFINITE;
     if (rinf <= tol) return UPD_CONVERGED;
+    if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_CONVERGED;
+    *rprev = (float)rinf;
     if (pass + 1 >= kmax) return UPD_NOCONV;
     if (pass + 1 == restart_pass) {
 #pragma unroll

@@ -173,3 +173,16 @@ def test_coupled1d_single_context_fp32c(S):
     assert np.max(np.abs(x - xo)) < 1e-4
     mo = O.moments(P, xo)
     assert abs(m[0, 0] - mo[0, 0]) < 1e-5 and abs((m[1, 0] - m[0, 0] ** 2) - (mo[1, 0] - mo[0, 0] ** 2)) < 1e-5
+
+
+@pytest.mark.parametrize("N,h", [(7, 2.0 ** -3), (50, 2.0 ** -4), (400, 2.0 ** -2)])
+def test_coupled3d_fp32c_large_h_small_n(S, N, h):
+    """FP32 pair sums where their evaluation floor exceeds 1e-10 (large h, small N):
+    the iteration stops at the floor and the run stays within the FP32 bar."""
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=9, precision=S.SSM_FP32C)
+    s.run()
+    x, _ = s.get_state()
+    s.close()
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=9)
+    xo = O.run(P, O.init_x0(P), 0, round(1.0 / h))
+    assert np.max(np.abs(x - xo)) < 1e-4
