@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 comparison (0 = skip)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batched", type=int, default=1, help="also time the 64-ensemble batched form (1/0)")
     p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
@@ -167,6 +168,41 @@ def run_reference(args, world, rank):
             "cpu_baseline": dict(cb, value=v, sample="%d random targets per step, full O(N) work each" % per),
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_descs(S):
+    """The 64-ensemble batched workload: N_e = round(2^(10 + 6 u_e)) with u_e the FP64
+    uniform of Philox(seed 3, counter (e, 0, 2, 0)), d_e = 1 for e < 32 else 3,
+    h_e = 2^-(4 + e mod 7), T = 1, seed 1000 + e."""
+    out = []
+    for e in range(64):
+        w = S.ssm_philox(3, [[e, 0, 2, 0]])[0]
+        u = (((int(w[0]) << 32 | int(w[1])) >> 11) + 1) * 2.0 ** -53
+        out.append(dict(d=1 if e < 32 else 3, N=int(round(2.0 ** (10 + 6 * u))), h=2.0 ** -(4 + e % 7), T=1.0,
+                        seed=1000 + e))
+    return out
+
+
+def bench_batched(torch, S, stream):
+    descs = batch_descs(S)
+    b = S.Batch(descs, stream=stream, precision=S.SSM_FP32C)
+    best = b.autotune()
+    units = sum(d["N"] * round(d["T"] / d["h"]) for d in descs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    b.run()                                  # one graph launch: every ensemble to T
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    dt = e0.elapsed_time(e1) / 1e3
+    st = b.stats()
+    res = {"value": units / dt, "unit": "particle-steps/s", "seconds": dt, "ensembles": len(descs),
+           "particle_steps": units, "N_range": [min(d["N"] for d in descs), max(d["N"] for d in descs)],
+           "batch_steps": st["batch_steps"], "newton_rows": st["newton_rows"], "plan": b.plan(),
+           "tuned_pass_ms": best, "graph_launches": 1}
+    b.close()
+    return res
 
 
 def time_kernel(torch, S, s, stream, which, reps):
@@ -327,6 +363,8 @@ def main():
                 "newton_passes_per_step": pst["newton_passes"] / max(1, pst["steps"])}
         p.close()
 
+    batched = bench_batched(torch, S, stream) if args.batched else None
+
     kmax = 12
     launches_per_step = 1 + 2 * kmax + 1 + 1 + 1 + 1 + (1 if form.startswith("learned") else 0)
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
@@ -342,6 +380,7 @@ def main():
             "fp32c_without_learned_start": fp32c_plain,
             "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
             "plain_fp64": fp64,
+            "batched_form": batched,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

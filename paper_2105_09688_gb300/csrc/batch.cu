@@ -208,7 +208,7 @@ __device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, in
     }
     Sw *= invN;
     const int r = newton_update_particle<D>(S, Sw, Y, X, E.h, E.tol, fp32, pass, kmax, -1, &E.rprev[i]);
-    if (r == UPD_CONTINUE)
+    if (r == UPD_CONTINUE || r == UPD_CONVERGED)
 #pragma unroll
         for (int c = 0; c < D; ++c) E.y[c * E.Np + i] = Y[c];
     return r;

@@ -231,7 +231,10 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
             passes[i] = pass + 1;
             atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
 #pragma unroll
-            for (int c = 0; c < D; ++c) sconv[c * Np + i] = S[c];
+            for (int c = 0; c < D; ++c) {
+                y[c * Np + i] = Y[c];
+                sconv[c * Np + i] = S[c];
+            }
         } else if (r == UPD_NOCONV || r == UPD_NONFINITE) {
             passes[i] = pass + 1;
             atomicOr(err, r == UPD_NOCONV ? ERR_NOCONV : ERR_NONFINITE);

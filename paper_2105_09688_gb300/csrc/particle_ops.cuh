@@ -17,11 +17,14 @@ enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 
 // a pair pass: S[D] = (1/N) sum_j (X_j - fl(Y)) w_j and Sw = (1/N) sum_j w_j were
 // evaluated at the current Y (fl = FP32 rounding when fp32_targets, exact
 // otherwise).  Forms the FP64 residual r = Y - X - h v(Y); if max|r| <= tol the
-// particle is done (S is returned in S_conv).  Otherwise Y moves to the root of
+// particle is done (Y and S stay).  Otherwise Y moves to the root of
 // the local model u = X + h(-u|u|^2 + 0.5(S - Sw (u - Y))): the cubic part exact,
 // the pair part linearised with the diagonal -Sw I of its Jacobian.  The local
 // Jacobian a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw) is inverted by
 // Sherman-Morrison; Newton on the local model converges to rounding in a few steps.
+// If a bound on the residual at that root is within tol, the particle is done
+// there (UPD_CONVERGED with Y moved): the pass that would only have verified it
+// is saved.
 //
 // FP32 pair sums can only certify the residual down to their evaluation floor
 // (rounding of the pair terms and of the FP32 target), which at large h or small
@@ -51,12 +54,6 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
     if (rinf <= tol) return UPD_CONVERGED;
     if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_CONVERGED;
     *rprev = (float)rinf;
-    if (pass + 1 >= kmax) return UPD_NOCONV;
-    if (pass + 1 == restart_pass) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) Y[c] = X[c];
-        return UPD_RESTART;
-    }
     double u[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) u[c] = Y[c];
@@ -81,6 +78,38 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
             umax = fmax(umax, fabs(u[c]));
         }
         if (smax <= 1e-16 * umax) break;
+    }
+    // Residual bound at u without another pair pass.  G(u) = 0 is the local model;
+    // r(u) - G(u) = -h/2 (S(u) - S(Y) + Sw (u - Y)), and by the mean value theorem
+    // |S(u) - S(Y) + Sw (u - Y)| <= (||2 M2|| + |grad Sw| |u - Y|) |u - Y| with
+    // M2 = (1/N) sum_j w_j^2 d_j d_j^T, ||2 M2|| <= 2 max_r r^2/(1+r^2)^2 = 1/2 and
+    // |grad Sw| <= 2 max_r r/(1+r^2)^2 < 0.65.  When the bound is within tol the
+    // particle is done at u (S is moved to u to first order for the record).
+    double uu = 0.0, du2 = 0.0, ginf = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) uu += u[c] * u[c];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double du = u[c] - Y[c];
+        const double g = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * du;
+        ginf = fmax(ginf, fabs(g));
+        du2 += du * du;
+    }
+    const double dn = sqrt(du2);
+    const double bound = 0.5 * h * (0.5 + 0.65 * dn) * dn + ginf;
+    if (bound <= tol) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            S[c] -= Sw * (u[c] - Y[c]);
+            Y[c] = u[c];
+        }
+        return UPD_CONVERGED;
+    }
+    if (pass + 1 >= kmax) return UPD_NOCONV;
+    if (pass + 1 == restart_pass) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) Y[c] = X[c];
+        return UPD_RESTART;
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) Y[c] = u[c];
