@@ -183,22 +183,26 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 
 template <int KIND>
 __device__ __forceinline__ void pair2(float2 sx, float2 sy, float2 sz, float2 ntx, float2 nty, float2 ntz,
-                                      float2 *acc);
+                                      float2 one, float2 *acc);
+// The differences and the plain sums are issued as FFMA2 with a unit factor
+// (fma(s, 1, -t) rounds exactly like s - t): FADD2 sustains only ~2/3 of the
+// FFMA2 rate on this SM.  `one` comes from shared memory so the compiler cannot
+// turn the fma back into an add.
 template <> __device__ __forceinline__ void pair2<PK_NEWTON3>(float2 sx, float2 sy, float2 sz, float2 ntx,
-                                                              float2 nty, float2 ntz, float2 *acc) {
-    const float2 dx = __fadd2_rn(sx, ntx), dy = __fadd2_rn(sy, nty), dz = __fadd2_rn(sz, ntz);
-    float2 q = __ffma2_rn(dx, dx, f2(1.0f, 1.0f));
+                                                              float2 nty, float2 ntz, float2 one, float2 *acc) {
+    const float2 dx = __ffma2_rn(sx, one, ntx), dy = __ffma2_rn(sy, one, nty), dz = __ffma2_rn(sz, one, ntz);
+    float2 q = __ffma2_rn(dx, dx, one);
     q = __ffma2_rn(dy, dy, q);
     q = __ffma2_rn(dz, dz, q);
     const float2 w = f2(rcp_approx(q.x), rcp_approx(q.y));
     acc[0] = __ffma2_rn(w, dx, acc[0]);
     acc[1] = __ffma2_rn(w, dy, acc[1]);
     acc[2] = __ffma2_rn(w, dz, acc[2]);
-    acc[3] = __fadd2_rn(acc[3], w);
+    acc[3] = __ffma2_rn(w, one, acc[3]);
 }
 template <> __device__ __forceinline__ void pair2<PK_DRIFT3>(float2 sx, float2 sy, float2 sz, float2 ntx,
-                                                             float2 nty, float2 ntz, float2 *acc) {
-    const float2 dx = __fadd2_rn(sx, ntx), dy = __fadd2_rn(sy, nty), dz = __fadd2_rn(sz, ntz);
+                                                             float2 nty, float2 ntz, float2 one, float2 *acc) {
+    const float2 dx = __ffma2_rn(sx, one, ntx), dy = __ffma2_rn(sy, one, nty), dz = __ffma2_rn(sz, one, ntz);
     const float2 mdz = f2(-dz.x, -dz.y), mdy = f2(-dy.x, -dy.y), mdx = f2(-dx.x, -dx.y);
     const float2 nq = __ffma2_rn(mdx, dx, __ffma2_rn(mdy, dy, __fmul2_rn(mdz, dz)));
     const float2 e = f2(ex2_approx(nq.x), ex2_approx(nq.y));
@@ -218,7 +222,9 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
     constexpr int NC = KindInfo<KIND>::NC, R2 = R / 2;
     __shared__ float4 sxy[SUB];   // (x, x, y, y)
     __shared__ float2 szz[SUB];   // (z, z)
+    __shared__ float2 s_one;
     const int tid = threadIdx.x;
+    if (tid == 0) s_one = f2(1.0f, 1.0f);
 
     float2 ntx[R2], nty[R2], ntz[R2];
 #pragma unroll
@@ -253,20 +259,23 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
             szz[s] = f2(z, z);
         }
         __syncthreads();
+        const float2 one = s_one;
         if (ns == SUB) {
 #pragma unroll 4
             for (int s = 0; s < SUB; ++s) {
                 const float4 a = sxy[s];
                 const float2 b = szz[s];
 #pragma unroll
-                for (int k = 0; k < R2; ++k) pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], acc[k]);
+                for (int k = 0; k < R2; ++k)
+                    pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], one, acc[k]);
             }
         } else {
             for (int s = 0; s < ns; ++s) {
                 const float4 a = sxy[s];
                 const float2 b = szz[s];
 #pragma unroll
-                for (int k = 0; k < R2; ++k) pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], acc[k]);
+                for (int k = 0; k < R2; ++k)
+                    pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], one, acc[k]);
             }
         }
 #pragma unroll
