@@ -29,7 +29,10 @@ sys.path.insert(0, ROOT)
 
 N_PART, DIM, H, T_END, SEED = 1 << 18, 3, 2.0 ** -8, 1.0, 2
 FP32_LANES_PER_SM, N_SMS, MAX_SM_MHZ = 128, 152, 2070.0
-# algorithmic FP32 flops per pair (FFMA = 2): see DESIGN.md, "Roofline"
+# Algorithmic FP32 flops per pair interaction (FFMA = 2, the special-function op
+# not counted): step-1 pair (x_j - y) / (1 + |x_j - y|^2) with its weight sum: 3
+# differences + 6 for 1 + |d|^2 + 6 for the weighted accumulation + 1 = 16; drift
+# pair (y_j - y) exp(-|d|^2 / 2): 3 differences + 5 for |d|^2 + 6 accumulation = 14.
 FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
 METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
 
@@ -149,7 +152,8 @@ def run_reference(args, world, rank):
     import oracle as O
     P = O.problem(d=DIM, coef=O.COEF_COUPLED3D, N=N_PART, h=H, seed=SEED)
     x = O.init_x0(P)
-    per = max(O.num_threads(), int(cb["value"] * max(1.0, 60.0 / max(1, args.steps + args.warmup)) / 4))
+    # each step a bounded sample: the K + W steps together take about --cpu-seconds
+    per = max(O.num_threads(), int(cb["value"] * max(1.0, args.cpu_seconds) / max(1, args.steps + args.warmup)))
     rng = np.random.default_rng(1)
     for k in range(args.warmup + args.steps):
         idx = rng.choice(N_PART, size=min(per, N_PART), replace=False)
@@ -159,7 +163,7 @@ def run_reference(args, world, rank):
         if k >= args.warmup:
             steps_s.append(idx.size / dt)
     v = statistics.median(steps_s)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_PART / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: X_0 ~ N(0, I_3) from Philox4x32-10 seed 2",
@@ -203,6 +207,17 @@ def bench_batched(torch, S, stream):
            "tuned_pass_ms": best, "graph_launches": 1}
     b.close()
     return res
+
+
+def aggregate_replicas(torch, world, local_seconds, local_units, device):
+    """Whole-job throughput of independent replicas: every rank's units over the
+    slowest rank's time (all-reduce MAX of the time; ranks hold equal work)."""
+    total = float(local_seconds)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    return total, world * local_units / total
 
 
 def time_kernel(torch, S, s, stream, which, reps):
@@ -277,12 +292,7 @@ def main():
     s.sync()
     st1 = s.stats()
     step_s = [a.elapsed_time(b) / 1e3 for a, b in evs]
-    total = float(sum(step_s))
-    if world > 1:
-        t = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * N_PART * args.steps / total
+    total, value = aggregate_replicas(torch, world, float(sum(step_s)), N_PART * args.steps, dev)
     newton_passes = (st1["newton_passes"] - st0["newton_passes"]) / args.steps
     newton_rows = (st1["newton_rows"] - st0["newton_rows"]) / args.steps
 
