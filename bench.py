@@ -34,6 +34,10 @@ FP32_LANES_PER_SM, N_SMS, MAX_SM_MHZ = 128, 152, 2070.0
 # differences + 6 for 1 + |d|^2 + 6 for the weighted accumulation + 1 = 16; drift
 # pair (y_j - y) exp(-|d|^2 / 2): 3 differences + 5 for |d|^2 + 6 accumulation = 14.
 FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
+# FP32 flops the centred-expansion kernels execute per pair (same sums, fewer
+# operations): step 1: 1 + 3 x 2 (q) + 3 x 2 + 1 = 14; drift: 3 x 2 + 3 x 2 + 1 = 13.
+FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
+FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
 METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
 
 
@@ -51,7 +55,11 @@ def parse():
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
     p.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"], help="form for --profile-kernels")
-    p.add_argument("--packed", type=int, default=0, help="--profile-kernels: use the packed-FP32 kernels")
+    p.add_argument("--packed", type=int, default=0, choices=[0, 1, 2],
+                   help="--profile-kernels: pair-kernel form (0 scalar, 1 packed difference form, 2 packed "
+                        "centred expansion)")
+    p.add_argument("--rpt", type=int, default=4, choices=[4, 8],
+                   help="--profile-kernels: targets per thread of the packed kernels (128 threads)")
     return p.parse_args()
 
 
@@ -64,8 +72,8 @@ def profile_kernels(args):
     prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
     s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec)
     if args.packed:
-        s.set_plan(0, 1, 128, 4)
-        s.set_plan(1, 1, 128, 4)
+        s.set_plan(0, args.packed, 128, args.rpt)
+        s.set_plan(1, args.packed, 128, args.rpt)
     s.step()
     s.pair_pass(0)
     s.pair_pass(1)
@@ -306,10 +314,14 @@ def main():
     sm_mhz = MAX_SM_MHZ
     peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / t_dom / 1e12
+    dom_form = plans["step1_pairs" if dom == 0 else "drift_pairs"]["form"]
+    executed = (FLOPS_PAIR_EXPANDED if dom_form == 2 else FLOPS_PAIR)[dom] * N_PART * N_PART / t_dom / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None,
-                "kernel": "%s<%s>" % ("k_pair2" if plans["step1_pairs" if dom == 0 else "drift_pairs"]["packed"]
-                                      else "k_pair", "PK_NEWTON3" if dom == 0 else "PK_DRIFT3"),
+                "kernel": "%s<%s> (%s)" % (("k_pair", "k_pair2", "k_pair2x")[dom_form],
+                                           "PK_NEWTON3" if dom == 0 else "PK_DRIFT3", FORM_NAMES[dom_form]),
+                "flops_per_pair": FLOPS_PAIR[dom],
+                "executed_tflops": executed, "executed_frac": executed / peak,
                 "peak_basis": "FP32 CUDA-core: 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe max clock)",
                 "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3}
 
@@ -337,7 +349,7 @@ def main():
                   precision=S.SSM_FP32C)
         for w in (0, 1):
             pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
-            q.set_plan(w, pl["packed"], pl["threads"], pl["targets_per_thread"])
+            q.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"])
         for _ in range(args.warmup):
             q.run_steps(1)
         q.sync()

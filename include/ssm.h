@@ -201,11 +201,14 @@ ssm_status ssm_pair_pass(ssm_ctx *ctx, int which, int64_t *pairs);
 ssm_status ssm_autotune(ssm_ctx *ctx, double *best_ms);
 
 /* The launch shape in use for which = 0 (step-1 sums) or 1 (drift):
- * out[5] = {packed (0/1), threads per block, targets per thread, chunks, sources per chunk}. */
+ * out[5] = {form, threads per block, targets per thread, chunks, sources per chunk},
+ * form 0 = scalar kernel, 1 = packed-FP32 difference form, 2 = packed-FP32 centred
+ * expansion (d = 3 FP32 forms only; same sums, fewer instructions per pair; a block
+ * whose targets lie far from the ensemble mean falls back to the difference form). */
 ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
 
-/* Select a launch shape explicitly: in[3] = {packed (0/1), threads per block,
- * targets per thread}; the chunk count is planned as in ssm_autotune.
+/* Select a launch shape explicitly: in[3] = {form (0/1/2 as in ssm_get_plan),
+ * threads per block, targets per thread}; the chunk count is planned as in ssm_autotune.
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
 
@@ -260,9 +263,16 @@ ssm_status ssm_batch_stats(ssm_batch *b, ssm_stats_t *out);
  * over all ensembles.  Leaves the state unchanged.  Synchronising. */
 ssm_status ssm_batch_autotune(ssm_batch *b, double *best_ms);
 
-/* Launch shape in use: out[5] = {packed d=3 kernel, threads, targets/thread d=1,
- * targets/thread d=3, sources per chunk}. */
+/* Launch shape in use: out[5] = {d=3 form (0 scalar, 1 packed difference form,
+ * 2 packed centred expansion), threads, targets/thread d=1, targets/thread d=3,
+ * sources per chunk}. */
 ssm_status ssm_batch_get_plan(ssm_batch *b, int *out);
+
+/* Select the launch shape explicitly: in[4] = {d=3 form (0/1/2 as in
+ * ssm_batch_get_plan), targets/thread d=1, targets/thread d=3, sources per chunk
+ * (4096, 8192 or 16384)}; rebuilds the graph.  The state is unchanged.
+ * SSM_EINVAL if that shape is not compiled for the batch's precision.  Synchronising. */
+ssm_status ssm_batch_set_plan(ssm_batch *b, const int *in);
 
 /* Release the batch and its device memory.  NULL-safe. */
 void ssm_batch_destroy(ssm_batch *b);

@@ -111,6 +111,7 @@ _SIGS = {
     "ssm_batch_stats": (_i32, [_vp, ctypes.POINTER(ssm_stats_t)]),
     "ssm_batch_autotune": (_i32, [_vp, _DP]),
     "ssm_batch_get_plan": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "ssm_batch_set_plan": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "ssm_batch_destroy": (None, [_vp]),
 }
 
@@ -172,10 +173,14 @@ class Batch:
         _check(lib().ssm_batch_autotune(self.b, ctypes.byref(best)), "ssm_batch_autotune")
         return float(best.value)
 
+    def set_plan(self, form, targets_per_thread_d1, targets_per_thread_d3, chunk_len):
+        arr = (_i32 * 4)(int(form), int(targets_per_thread_d1), int(targets_per_thread_d3), int(chunk_len))
+        _check(lib().ssm_batch_set_plan(self.b, arr), "ssm_batch_set_plan")
+
     def plan(self):
         out = (_i32 * 5)()
         _check(lib().ssm_batch_get_plan(self.b, out), "ssm_batch_get_plan")
-        return dict(zip(("packed", "threads", "targets_per_thread_d1", "targets_per_thread_d3", "chunk_len"),
+        return dict(zip(("form", "threads", "targets_per_thread_d1", "targets_per_thread_d3", "chunk_len"),
                         list(out)))
 
     def close(self):
@@ -396,11 +401,12 @@ def ssm_autotune(ctx):
 def ssm_get_plan(ctx, which):
     out = (_i32 * 5)()
     _check(lib().ssm_get_plan(ctx, int(which), out), "ssm_get_plan")
-    return dict(zip(("packed", "threads", "targets_per_thread", "chunks", "chunk_len"), list(out)))
+    return dict(zip(("form", "threads", "targets_per_thread", "chunks", "chunk_len"), list(out)))
 
 
-def ssm_set_plan(ctx, which, packed, threads, targets_per_thread):
-    arr = (_i32 * 3)(int(bool(packed)), int(threads), int(targets_per_thread))
+def ssm_set_plan(ctx, which, form, threads, targets_per_thread):
+    """form: 0 scalar kernel, 1 packed-FP32 difference form, 2 packed-FP32 centred expansion."""
+    arr = (_i32 * 3)(int(form), int(threads), int(targets_per_thread))
     _check(lib().ssm_set_plan(ctx, int(which), arr), "ssm_set_plan")
 
 
@@ -481,8 +487,8 @@ class SSM:
     def plan(self, which):
         return ssm_get_plan(self.ctx, which)
 
-    def set_plan(self, which, packed, threads, targets_per_thread):
-        ssm_set_plan(self.ctx, which, packed, threads, targets_per_thread)
+    def set_plan(self, which, form, threads, targets_per_thread):
+        ssm_set_plan(self.ctx, which, form, threads, targets_per_thread)
 
     def ws_load(self, blob):
         ssm_ws_load(self.ctx, blob)

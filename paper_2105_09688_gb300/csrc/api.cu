@@ -13,10 +13,6 @@
 #include "ssm_device.cuh"
 
 namespace ssm {
-cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
-                      const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st);
-int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt);
-int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out);
 cudaError_t launch_init_x0(ssm_ctx *c);
 cudaError_t launch_moments(ssm_ctx *c);
 cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st);
@@ -74,7 +70,7 @@ int newton_kind(int d) { return d == 1 ? PK_NEWTON1 : PK_NEWTON3; }
 int drift_kind(int coef) { return (coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM_COEF_COUPLED1D) ? PK_DRIFT1 : PK_DRIFT3; }
 
 // Resident-block slots of the device for a pair kernel shape (0 = no device).
-int device_slots(int kind, bool fp32, bool vec2, int threads, int rpt) {
+int device_slots(int kind, bool fp32, int vec2, int threads, int rpt) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); return 0; }
@@ -125,7 +121,7 @@ Plan make_plan_shape(int64_t N, int kind, int vec2, int threads, int rpt, int fo
 // 8 (FP32 d=1) or 2 (FP64) targets per thread; chunks from the device's slots.
 Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
     const int th = 128, r = fp32 ? (kind == PK_DRIFT1 ? 8 : 4) : 2;
-    return make_plan_shape(N, kind, 0, th, r, force_chunks, device_slots(kind, fp32, false, th, r));
+    return make_plan_shape(N, kind, 0, th, r, force_chunks, device_slots(kind, fp32, 0, th, r));
 }
 
 struct Layout {
@@ -263,15 +259,15 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if ((e = ws_forward_start(c)) != cudaSuccess) return e;
     int *a_in = c->act0, *a_out = c->act1;
     for (int k = 0; k < c->kmax; ++k) {
-        if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0, c->part,
-                           c->st)) != cudaSuccess)
+        if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0,
+                           c->part, c->st)) != cudaSuccess)
             return e;
         if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
         int *t = a_in; a_in = a_out; a_out = t;
     }
     if ((e = launch_step_stats(c)) != cudaSuccess) return e;
-    if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale, c->part,
-                       c->st)) != cudaSuccess)
+    if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale,
+                       c->part, c->st)) != cudaSuccess)
         return e;
     return launch_euler(c, bscale);
 }
@@ -542,8 +538,8 @@ ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
     const bool f32 = fp32_pairs(c);
     cudaError_t e;
     if (which == 0) {
-        e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0, c->part,
-                      c->st);
+        e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0,
+                      c->part, c->st);
     } else {
         double scale, bscale;
         drift_scale(c->coef, f32, c->N, &scale, &bscale);
@@ -579,7 +575,7 @@ ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
         Plan best = q == 0 ? c->plan_newton : c->plan_drift;
         float best_t = 1e30f;
         for (int k = 0; k < nc && err == cudaSuccess; ++k) {
-            const int slots = device_slots(kind, f32, cand[k][0] != 0, cand[k][1], cand[k][2]);
+            const int slots = device_slots(kind, f32, cand[k][0], cand[k][1], cand[k][2]);
             if (slots <= 0) continue;
             Plan p = make_plan_shape(c->N, kind, cand[k][0], cand[k][1], cand[k][2], c->opt.tile_chunks, slots);
             err = pair_sums(kind, f32, p, src, c->y, nullptr, nullptr, c->N, c->Np, sc, c->part, c->st);
@@ -618,10 +614,10 @@ ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
     const int nc = pair_shape_candidates(kind, f32, cand, 32);
     bool ok = false;
     for (int k = 0; k < nc; ++k)
-        if (cand[k][0] == (in[0] != 0) && cand[k][1] == in[1] && cand[k][2] == in[2]) ok = true;
+        if (cand[k][0] == in[0] && cand[k][1] == in[1] && cand[k][2] == in[2]) ok = true;
     if (!ok) return SSM_EINVAL;
-    const int slots = device_slots(kind, f32, in[0] != 0, in[1], in[2]);
-    Plan p = make_plan_shape(c->N, kind, in[0] != 0, in[1], in[2], c->opt.tile_chunks, slots);
+    const int slots = device_slots(kind, f32, in[0], in[1], in[2]);
+    Plan p = make_plan_shape(c->N, kind, in[0], in[1], in[2], c->opt.tile_chunks, slots);
     if (which == 0) c->plan_newton = p; else c->plan_drift = p;
     if (c->graph_ready) { cudaGraphExecDestroy(c->gexec); c->graph_ready = false; }
     return SSM_OK;

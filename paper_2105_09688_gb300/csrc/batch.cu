@@ -63,7 +63,8 @@ struct BGlobal {             // batch-wide device state
     long long counters[CNT_N];
 };
 
-struct BShape { int r1, r3, packed; };   // targets per thread (d = 1, d = 3), packed d = 3 kernel
+struct BShape { int r1, r3, packed; };   // targets per thread (d = 1, d = 3); d = 3 form: 0 scalar,
+                                         // 1 packed difference form, 2 packed centred expansion
 
 // ---- block-wide prefix sum over ensembles (every block computes the same) ----
 template <typename F>
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(SEGT) kb_plain_start(BEns *ens, int n_ens, BGl
 
 // Pair sums of all ensembles: step-1 sums (NEWTON) at the active targets of the
 // current pass, or the drift sums at all particles.
-template <bool NEWTON, typename T, int R1, int R3, bool PK3>
+template <bool NEWTON, typename T, int R1, int R3, int PK3>
 __global__ void __launch_bounds__(BT)
 kb_pair(BEns *ens, int n_ens, const BGlobal *g) {
     __shared__ long long pref[MAX_ENS + 1];
@@ -178,8 +179,8 @@ kb_pair(BEns *ens, int n_ens, const BGlobal *g) {
             tile_scalar<NEWTON ? PK_NEWTON1 : PK_DRIFT1, T, BT, R1>(src, E.y, act, ntgt, E.Np, j0, j1,
                                                                      tile * BT * R1, sc, part);
         } else if (PK3) {
-            tile_packed<NEWTON ? PK_NEWTON3 : PK_DRIFT3, BT, R3>(src, E.y, act, ntgt, E.Np, j0, j1, tile * BT * R3,
-                                                                 sc, part);
+            tile_packed<NEWTON ? PK_NEWTON3 : PK_DRIFT3, BT, R3, PK3 == 2>(src, E.y, act, ntgt, E.Np, j0, j1,
+                                                                           tile * BT * R3, sc, part);
         } else {
             tile_scalar<NEWTON ? PK_NEWTON3 : PK_DRIFT3, T, BT, R3>(src, E.y, act, ntgt, E.Np, j0, j1,
                                                                      tile * BT * R3, sc, part);
@@ -355,16 +356,18 @@ __global__ void kb_finish(BEns *ens, int n_ens, const long long *seg_pref, const
 
 __global__ void kb_set_stop(BGlobal *g, long long k) { g->stop_at = g->bstep + k; }
 
-constexpr BShape SHAPES_F32[] = { {8, 4, 1}, {8, 8, 1}, {8, 4, 0}, {4, 4, 0} };
+constexpr BShape SHAPES_F32[] = { {8, 4, 1}, {8, 8, 1}, {8, 4, 2}, {8, 8, 2}, {8, 4, 0}, {4, 4, 0} };
 constexpr BShape SHAPE_F64 = {2, 2, 0};
 
 template <bool NEWTON>
 void *pair_kernel(bool f32, const BShape &s) {
-    if (!f32) return (void *)kb_pair<NEWTON, double, 2, 2, false>;
-    if (s.packed && s.r3 == 4) return (void *)kb_pair<NEWTON, float, 8, 4, true>;
-    if (s.packed && s.r3 == 8) return (void *)kb_pair<NEWTON, float, 8, 8, true>;
-    if (s.r1 == 8) return (void *)kb_pair<NEWTON, float, 8, 4, false>;
-    return (void *)kb_pair<NEWTON, float, 4, 4, false>;
+    if (!f32) return (void *)kb_pair<NEWTON, double, 2, 2, 0>;
+    if (s.packed == 1 && s.r3 == 4) return (void *)kb_pair<NEWTON, float, 8, 4, 1>;
+    if (s.packed == 1 && s.r3 == 8) return (void *)kb_pair<NEWTON, float, 8, 8, 1>;
+    if (s.packed == 2 && s.r3 == 4) return (void *)kb_pair<NEWTON, float, 8, 4, 2>;
+    if (s.packed == 2 && s.r3 == 8) return (void *)kb_pair<NEWTON, float, 8, 8, 2>;
+    if (s.r1 == 8) return (void *)kb_pair<NEWTON, float, 8, 4, 0>;
+    return (void *)kb_pair<NEWTON, float, 4, 4, 0>;
 }
 
 }  // namespace
@@ -500,6 +503,14 @@ void set_grids(ssm_batch *b) {
     b->grid_pair[0] = resident_grid(pair_kernel<true>(b->f32, b->shape), BT);
     b->grid_pair[1] = resident_grid(pair_kernel<false>(b->f32, b->shape), BT);
     b->grid_small = resident_grid((void *)kb_update, SEGT);
+}
+
+// Refresh the host copy of the ensemble descriptors from the device (the step
+// counters and active flags advance there) before editing and re-uploading it.
+cudaError_t pull_ens(ssm_batch *b) {
+    cudaError_t e = cudaMemcpyAsync(b->h_ens.data(), b->d_ens, sizeof(BEns) * b->n, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    return e;
 }
 
 ssm_status harvest_batch(ssm_batch *b) {
@@ -711,9 +722,10 @@ ssm_status ssm_batch_autotune(ssm_batch *b, double *best_ms) {
     if (b->f32) for (const BShape &s : SHAPES_F32) cands.push_back(s);
     else cands.push_back(SHAPE_F64);
     const int64_t lens[3] = { 4096, 8192, 16384 };
+    cudaError_t err = pull_ens(b);
+    if (err != cudaSuccess) { b->status = cuda_st(err); return (ssm_status)b->status; }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SSM_ECUDA;
-    cudaError_t err = cudaSuccess;
     float best = 1e30f;
     BShape best_s = b->shape;
     int64_t best_len = b->chunk_len;
@@ -754,6 +766,30 @@ ssm_status ssm_batch_autotune(ssm_batch *b, double *best_ms) {
     if (err == cudaSuccess) err = cudaStreamSynchronize(b->st);
     if (err != cudaSuccess) { b->status = cuda_st(err); return (ssm_status)b->status; }
     if (best_ms) *best_ms = best;
+    return SSM_OK;
+}
+
+ssm_status ssm_batch_set_plan(ssm_batch *b, const int *in) {
+    if (!b || !in) return SSM_EINVAL;
+    if (b->status != SSM_OK) return (ssm_status)b->status;
+    bool ok = false;
+    BShape shape = SHAPE_F64;
+    if (b->f32) {
+        for (const BShape &s : SHAPES_F32)
+            if (s.packed == in[0] && s.r1 == in[1] && s.r3 == in[2]) { ok = true; shape = s; }
+    } else {
+        ok = SHAPE_F64.packed == in[0] && SHAPE_F64.r1 == in[1] && SHAPE_F64.r3 == in[2];
+    }
+    if (!ok || (in[3] != 4096 && in[3] != 8192 && in[3] != 16384)) return SSM_EINVAL;
+    cudaError_t err = pull_ens(b);
+    if (err == cudaSuccess) {
+        b->shape = shape;
+        set_chunks(b, in[3]);
+        err = cudaMemcpyAsync(b->d_ens, b->h_ens.data(), sizeof(BEns) * b->n, cudaMemcpyHostToDevice, b->st);
+    }
+    if (err == cudaSuccess) { set_grids(b); err = build_graph(b); }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(b->st);
+    if (err != cudaSuccess) { b->status = cuda_st(err); return (ssm_status)b->status; }
     return SSM_OK;
 }
 

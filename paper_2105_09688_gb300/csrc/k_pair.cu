@@ -35,8 +35,23 @@ k_pair2(const double *__restrict__ src, const double *__restrict__ tgt, const in
     if (t0 >= ntgt) return;
     const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
     const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
-    tile_packed<KIND, THREADS, R>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
-                                  part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
+    tile_packed<KIND, THREADS, R, false>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
+                                         part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
+}
+
+// Centred expansion where a block's targets allow it (difference form otherwise).
+template <int KIND, int THREADS, int R>
+__global__ void __launch_bounds__(THREADS, packed_min_blocks(THREADS, R))
+k_pair2x(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
+         const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
+         double *__restrict__ part) {
+    const int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
+    if (t0 >= ntgt) return;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
+    const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
+    tile_packed<KIND, THREADS, R, true>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
+                                        part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
 }
 
 template <int KIND, typename T, int THREADS, int R>
@@ -52,7 +67,10 @@ static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, 
                            int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
     const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)p.chunks);
-    k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+    if (p.vec2 == 2)
+        k_pair2x<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+    else
+        k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
     return cudaGetLastError();
 }
 
@@ -111,12 +129,14 @@ static int occ_dispatch(int threads, int rpt) {
 #undef SSM_CASE
     return 0;
 }
-template <int KIND>
+template <int KIND, bool EXPAND>
 static int occ_dispatch2(int threads, int rpt) {
     int nb = 0;
 #define SSM_CASE(TH, RR) \
     if (threads == TH && rpt == RR) { \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair2<KIND, TH, RR>, TH, 0) != cudaSuccess) nb = 0; \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, EXPAND ? (const void *)k_pair2x<KIND, TH, RR> \
+                                                          : (const void *)k_pair2<KIND, TH, RR>, TH, 0) != cudaSuccess) \
+            nb = 0; \
         return nb; }
     SSM_PAIR2_SHAPES(SSM_CASE)
 #undef SSM_CASE
@@ -124,10 +144,12 @@ static int occ_dispatch2(int threads, int rpt) {
 }
 
 // Resident blocks per SM of a pair kernel shape (0 if unknown / no device).
-int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt) {
+int pair_blocks_per_sm(int kind, bool fp32, int vec2, int threads, int rpt) {
     if (fp32 && vec2) {
-        if (kind == PK_NEWTON3) return occ_dispatch2<PK_NEWTON3>(threads, rpt);
-        if (kind == PK_DRIFT3) return occ_dispatch2<PK_DRIFT3>(threads, rpt);
+        if (kind == PK_NEWTON3)
+            return vec2 == 2 ? occ_dispatch2<PK_NEWTON3, true>(threads, rpt) : occ_dispatch2<PK_NEWTON3, false>(threads, rpt);
+        if (kind == PK_DRIFT3)
+            return vec2 == 2 ? occ_dispatch2<PK_DRIFT3, true>(threads, rpt) : occ_dispatch2<PK_DRIFT3, false>(threads, rpt);
         return 0;
     }
 #define SSM_KIND(K) case K: return fp32 ? occ_dispatch<K, float>(threads, rpt) : occ_dispatch<K, double>(threads, rpt);
@@ -141,7 +163,8 @@ int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt) {
     return 0;
 }
 
-// Candidate launch shapes of a pair kind for the autotuner: {vec2, threads, rpt}.
+// Candidate launch shapes of a pair kind for the autotuner: {vec2, threads, rpt}
+// (vec2: 0 scalar, 1 packed difference form, 2 packed centred expansion).
 int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out) {
     int n = 0;
     auto add = [&](int v, int th, int r) { if (n < max_out) { out[n][0] = v; out[n][1] = th; out[n][2] = r; ++n; } };
@@ -149,7 +172,7 @@ int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out) {
     SSM_PAIR_SHAPES(SSM_CASE)
 #undef SSM_CASE
     if (fp32 && (kind == PK_NEWTON3 || kind == PK_DRIFT3)) {
-#define SSM_CASE(TH, RR) add(1, TH, RR);
+#define SSM_CASE(TH, RR) add(1, TH, RR); add(2, TH, RR);
         SSM_PAIR2_SHAPES(SSM_CASE)
 #undef SSM_CASE
     }

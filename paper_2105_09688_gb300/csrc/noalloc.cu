@@ -32,12 +32,6 @@
 #include "ssm.h"
 #include "ssm_device.cuh"
 
-namespace ssm {
-cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
-                      const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st);
-int pair_blocks_per_sm(int kind, bool fp32, bool vec2, int threads, int rpt);
-}  // namespace ssm
-
 using namespace ssm;
 
 namespace {
@@ -103,7 +97,7 @@ extern "C" ssm_status ssm_drift_noalloc(int coef, int precision, int64_t N, cons
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SSM_ECUDA;
-    const int nb = pair_blocks_per_sm(kind, f32, false, p.threads, p.rpt);
+    const int nb = pair_blocks_per_sm(kind, f32, 0, p.threads, p.rpt);
     const int64_t tiles = (N + p.threads * p.rpt - 1) / (p.threads * p.rpt);
     int64_t want = nb > 0 ? (4LL * sms * nb + tiles - 1) / tiles : 1;
     const int64_t fit = SCRATCH_DOUBLES / ((int64_t)d * ld);

@@ -178,9 +178,13 @@ __device__ __forceinline__ void tile_scalar(const double *__restrict__ src, cons
     }
 }
 
-// ---- packed FP32 form (d = 3 kinds) -----------------------------------------
+// ---- packed FP32 forms (d = 3 kinds) ----------------------------------------
+// Target 2k of a register pair in .x, 2k+1 in .y; a source value is stored
+// duplicated in shared memory so one packed instruction advances two pair
+// interactions.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Difference form: the scalar FP32 arithmetic, term for term.
 template <int KIND>
 __device__ __forceinline__ void pair2(float2 sx, float2 sy, float2 sz, float2 ntx, float2 nty, float2 ntz,
                                       float2 one, float2 *acc);
@@ -211,20 +215,82 @@ template <> __device__ __forceinline__ void pair2<PK_DRIFT3>(float2 sx, float2 s
     acc[2] = __ffma2_rn(e, dz, acc[2]);
 }
 
-// Packed tile: target 2k of a register pair in .x, 2k+1 in .y; a source coordinate
-// is stored duplicated in shared memory so one packed instruction advances two
-// pair interactions.  Same arithmetic as the scalar FP32 form, term for term.
+// Centred expansion.  With s = scale (x_j - c) and t = scale (y_i - c) rounded to
+// FP32, c a point near the block's targets (their centroid),
+//   1 + |s - t|^2  = (1 + |s|^2) + |t|^2 - 2 s.t                  (step 1, scale 1)
+//   2^(-|s - t|^2) = 2^(-|t|^2) * 2^(-|s|^2 + 2 s.t)                  (drift)
+// and sum_j w_ij (s_j - t_i) = sum_j w_ij s_j - t_i sum_j w_ij.  So a pair costs the
+// dot product and four accumulations -- 8 (step 1) and 7 (drift) packed
+// instructions instead of 10 and 9 -- and the per-target factors (|t|^2, 2^(-|t|^2)
+// and the linear t_i term) are applied once per target in FP64.  The source record
+// is (s, k_j) with k_j = 1 + |s_j|^2 (step 1) or -|s_j|^2 (drift); the target
+// registers hold u = -2t (step 1) or 2t (drift) and, for step 1, kb = |t|^2.
+template <int KIND>
+__device__ __forceinline__ void pair2x(float2 sx, float2 sy, float2 sz, float2 k, float2 ux, float2 uy, float2 uz,
+                                       float2 kb, float2 one, float2 *acc);
+template <> __device__ __forceinline__ void pair2x<PK_NEWTON3>(float2 sx, float2 sy, float2 sz, float2 k, float2 ux,
+                                                               float2 uy, float2 uz, float2 kb, float2 one,
+                                                               float2 *acc) {
+    float2 q = __ffma2_rn(k, one, kb);
+    q = __ffma2_rn(sz, uz, q);
+    q = __ffma2_rn(sy, uy, q);
+    q = __ffma2_rn(sx, ux, q);
+    const float2 w = f2(rcp_approx(q.x), rcp_approx(q.y));
+    acc[0] = __ffma2_rn(w, sx, acc[0]);
+    acc[1] = __ffma2_rn(w, sy, acc[1]);
+    acc[2] = __ffma2_rn(w, sz, acc[2]);
+    acc[3] = __ffma2_rn(w, one, acc[3]);
+}
+template <> __device__ __forceinline__ void pair2x<PK_DRIFT3>(float2 sx, float2 sy, float2 sz, float2 k, float2 ux,
+                                                              float2 uy, float2 uz, float2, float2 one, float2 *acc) {
+    float2 g = __ffma2_rn(sz, uz, k);
+    g = __ffma2_rn(sy, uy, g);
+    g = __ffma2_rn(sx, ux, g);
+    const float2 e = f2(ex2_approx(g.x), ex2_approx(g.y));
+    acc[0] = __ffma2_rn(e, sx, acc[0]);
+    acc[1] = __ffma2_rn(e, sy, acc[1]);
+    acc[2] = __ffma2_rn(e, sz, acc[2]);
+    acc[3] = __ffma2_rn(e, one, acc[3]);
+}
+
+// Cancellation in the expansion grows with |s|^2 + |t|^2 (the rounding of one
+// pair term is ~2^-24 (1 + 2|s|^2 + 2|t|^2) / q relative), so a block takes the
+// expansion only when every one of its targets has |t|^2 <= EXP_R2 (scaled units
+// about the centre); a source far from all targets makes q or the exponent large
+// itself and keeps ~2^-24 relative accuracy.  The bound also keeps the drift's
+// 2^(-|s|^2 + 2 s.t) <= 2^|t|^2 far from FP32 overflow.
+constexpr float EXP_R2 = 64.f;
+
+template <int KIND> struct PackedInfo;   // accumulators per target: difference / expanded form
+template <> struct PackedInfo<PK_NEWTON3> { static constexpr int NC = 4, NX = 4; };
+template <> struct PackedInfo<PK_DRIFT3> { static constexpr int NC = 3, NX = 4; };
+
+__device__ __forceinline__ int64_t target_index(const int *__restrict__ act, int64_t t, int64_t ntgt) {
+    return t < ntgt ? (act ? (int64_t)act[t] : t) : 0;
+}
+
+template <int NC, int R2>
+__device__ __forceinline__ void fold_subtile(float2 (&acc)[R2][NC], float2 (&hi)[R2][NC], float2 (&lo)[R2][NC]) {
+#pragma unroll
+    for (int k = 0; k < R2; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            two_sum_acc(hi[k][c].x, lo[k][c].x, acc[k][c].x);
+            two_sum_acc(hi[k][c].y, lo[k][c].y, acc[k][c].y);
+            acc[k][c] = f2(0.f, 0.f);
+        }
+}
+
+// Difference form of a packed tile (buf: 2*SUB float4 of shared memory).
 template <int KIND, int THREADS, int R>
-__device__ __forceinline__ void tile_packed(const double *__restrict__ src, const double *__restrict__ tgt,
-                                            const int *__restrict__ act, int64_t ntgt, int64_t Np, int64_t j0,
-                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part) {
-    static_assert(R % 2 == 0, "targets per thread come in pairs");
-    constexpr int NC = KindInfo<KIND>::NC, R2 = R / 2;
-    __shared__ float4 sxy[SUB];   // (x, x, y, y)
-    __shared__ float2 szz[SUB];   // (z, z)
-    __shared__ float2 s_one;
+__device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_one, const double *__restrict__ src,
+                                                 const double *__restrict__ tgt, const int *__restrict__ act,
+                                                 int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
+                                                 double scale, double *__restrict__ part) {
+    constexpr int NC = PackedInfo<KIND>::NC, R2 = R / 2;
+    float4 *sxy = buf;                              // (x, x, y, y)
+    float2 *szz = reinterpret_cast<float2 *>(buf + SUB);   // (z, z)
     const int tid = threadIdx.x;
-    if (tid == 0) s_one = f2(1.0f, 1.0f);
 
     float2 ntx[R2], nty[R2], ntz[R2];
 #pragma unroll
@@ -232,9 +298,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
         float v[2][3];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t t = t0 + (2 * k + e) * THREADS + tid;
-            int64_t i = 0;
-            if (t < ntgt) i = act ? (int64_t)act[t] : t;
+            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt);
             v[e][0] = -(float)(tgt[i] * scale);
             v[e][1] = -(float)(tgt[Np + i] * scale);
             v[e][2] = -(float)(tgt[2 * Np + i] * scale);
@@ -259,7 +323,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
             szz[s] = f2(z, z);
         }
         __syncthreads();
-        const float2 one = s_one;
+        const float2 one = *s_one;
         if (ns == SUB) {
 #pragma unroll 4
             for (int s = 0; s < SUB; ++s) {
@@ -278,14 +342,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
                     pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], one, acc[k]);
             }
         }
-#pragma unroll
-        for (int k = 0; k < R2; ++k)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                two_sum_acc(hi[k][c].x, lo[k][c].x, acc[k][c].x);
-                two_sum_acc(hi[k][c].y, lo[k][c].y, acc[k][c].y);
-                acc[k][c] = f2(0.f, 0.f);
-            }
+        fold_subtile<NC, R2>(acc, hi, lo);
     }
 #pragma unroll
     for (int k = 0; k < R2; ++k)
@@ -299,6 +356,186 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
                         e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
             }
         }
+}
+
+// Expanded form of a packed tile about the point cc[3] (unscaled coordinates).
+// The partial sums it writes mean what the difference form's mean:
+//   step 1: sum_j w (s_j - fl(y_i)) and sum_j w, with s_j = fl(x_j - c) + c, so the
+//           consumer's correction of the FP32 target, -(y - fl(y)) sum w, still
+//           applies (the linear t_i term is taken in FP64 here);
+//   drift : sum_j e_ij (s_j - t_i) in scaled units, t_i = scale (y_i - c) exact.
+template <int KIND, int THREADS, int R>
+__device__ __forceinline__ void tile_packed_exp(float4 *buf, const float2 *s_one, const double *__restrict__ src,
+                                                const double *__restrict__ tgt, const int *__restrict__ act,
+                                                int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
+                                                double scale, const double (&cc)[3], double *__restrict__ part) {
+    constexpr bool NEWTON = KIND == PK_NEWTON3;
+    constexpr int NX = PackedInfo<KIND>::NX, R2 = R / 2;
+    const int tid = threadIdx.x;
+    const float usign = NEWTON ? -2.f : 2.f;
+
+    float2 ux[R2], uy[R2], uz[R2], kb[R2];
+#pragma unroll
+    for (int k = 0; k < R2; ++k) {
+        float v[2][4];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt);
+            const float a = (float)((tgt[i] - cc[0]) * scale), b = (float)((tgt[Np + i] - cc[1]) * scale),
+                        d = (float)((tgt[2 * Np + i] - cc[2]) * scale);
+            v[e][0] = usign * a;
+            v[e][1] = usign * b;
+            v[e][2] = usign * d;
+            v[e][3] = (float)((double)a * a + (double)b * b + (double)d * d);
+        }
+        ux[k] = f2(v[0][0], v[1][0]);
+        uy[k] = f2(v[0][1], v[1][1]);
+        uz[k] = f2(v[0][2], v[1][2]);
+        kb[k] = f2(v[0][3], v[1][3]);
+    }
+    float2 acc[R2][NX], hi[R2][NX], lo[R2][NX];
+#pragma unroll
+    for (int k = 0; k < R2; ++k)
+#pragma unroll
+        for (int c = 0; c < NX; ++c) { acc[k][c] = f2(0.f, 0.f); hi[k][c] = f2(0.f, 0.f); lo[k][c] = f2(0.f, 0.f); }
+
+    for (int64_t base = j0; base < j1; base += SUB) {
+        const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
+        __syncthreads();
+        for (int s = tid; s < ns; s += THREADS) {
+            const int64_t j = base + s;
+            const float x = (float)((src[j] - cc[0]) * scale), y = (float)((src[Np + j] - cc[1]) * scale),
+                        z = (float)((src[2 * Np + j] - cc[2]) * scale);
+            const double n2 = (double)x * x + (double)y * y + (double)z * z;
+            const float kj = NEWTON ? (float)(1.0 + n2) : (float)(-n2);
+            buf[2 * s] = make_float4(x, x, y, y);
+            buf[2 * s + 1] = make_float4(z, z, kj, kj);
+        }
+        __syncthreads();
+        const float2 one = *s_one;
+        if (ns == SUB) {
+#pragma unroll 8
+            for (int s = 0; s < SUB; ++s) {
+                const float4 a = buf[2 * s], b = buf[2 * s + 1];
+#pragma unroll
+                for (int k = 0; k < R2; ++k)
+                    pair2x<KIND>(f2(a.x, a.y), f2(a.z, a.w), f2(b.x, b.y), f2(b.z, b.w), ux[k], uy[k], uz[k], kb[k],
+                                 one, acc[k]);
+            }
+        } else {
+            for (int s = 0; s < ns; ++s) {
+                const float4 a = buf[2 * s], b = buf[2 * s + 1];
+#pragma unroll
+                for (int k = 0; k < R2; ++k)
+                    pair2x<KIND>(f2(a.x, a.y), f2(a.z, a.w), f2(b.x, b.y), f2(b.z, b.w), ux[k], uy[k], uz[k], kb[k],
+                                 one, acc[k]);
+            }
+        }
+        fold_subtile<NX, R2>(acc, hi, lo);
+    }
+#pragma unroll
+    for (int k = 0; k < R2; ++k)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t t = t0 + (2 * k + e) * THREADS + tid;
+            if (t < ntgt) {
+                const int64_t i = act ? (int64_t)act[t] : t;
+                double S[NX];
+#pragma unroll
+                for (int c = 0; c < NX; ++c)
+                    S[c] = e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
+                if (NEWTON) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double yc = tgt[c * Np + i];
+                        part[(int64_t)c * Np + t] = S[c] - ((double)(float)yc - cc[c]) * S[3];
+                    }
+                    part[(int64_t)3 * Np + t] = S[3];
+                } else {
+                    const float2 tu[3] = {ux[k], uy[k], uz[k]};
+                    double b2 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double tc = 0.5 * (double)(e == 0 ? tu[c].x : tu[c].y);   // the FP32 t_i
+                        b2 += tc * tc;
+                    }
+                    const double f = exp2(-b2);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        part[(int64_t)c * Np + t] = f * (S[c] - (tgt[c * Np + i] - cc[c]) * scale * S[3]);
+                }
+            }
+        }
+}
+
+// Resident blocks per SM that the expanded kernels are compiled for (the register
+// budget ptxas schedules the loop under; chosen by timing the compiled shapes).
+__host__ __device__ constexpr int packed_min_blocks(int threads, int r) {
+    return threads == 128 ? (r == 8 ? 3 : 5) : (r == 8 ? 1 : 2);
+}
+
+// Packed tile.  EXPAND: the block centres the expansion on the centroid of its
+// own targets and takes it when all of them are within EXP_R2 of that point,
+// else it runs the difference form; the choice is block-uniform and depends only
+// on the data (and the launch shape).
+template <int KIND, int THREADS, int R, bool EXPAND>
+__device__ __forceinline__ void tile_packed(const double *__restrict__ src, const double *__restrict__ tgt,
+                                            const int *__restrict__ act, int64_t ntgt, int64_t Np, int64_t j0,
+                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part) {
+    static_assert(R % 2 == 0, "targets per thread come in pairs");
+    static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
+    __shared__ float4 buf[2 * SUB];
+    __shared__ float2 s_one;
+    __shared__ double s_red[THREADS / 32][4];
+    const int tid = threadIdx.x;
+    if (tid == 0) s_one = f2(1.0f, 1.0f);
+    if (EXPAND) {
+        // centroid of the valid targets (fixed-order FP64 reduction)
+        double m[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t t = t0 + r * THREADS + tid;
+            if (t < ntgt) {
+                const int64_t i = act ? (int64_t)act[t] : t;
+                m[0] += tgt[i];
+                m[1] += tgt[Np + i];
+                m[2] += tgt[2 * Np + i];
+                m[3] += 1.0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+        if ((tid & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_red[tid >> 5][k] = m[k];
+        __syncthreads();
+        double cc[3] = {0.0, 0.0, 0.0}, cnt = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) {
+            cc[0] += s_red[w][0];
+            cc[1] += s_red[w][1];
+            cc[2] += s_red[w][2];
+            cnt += s_red[w][3];
+        }
+        cc[0] /= cnt; cc[1] /= cnt; cc[2] /= cnt;   // cnt >= 1: the caller skips empty tiles
+        int ok = 1;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t t = t0 + r * THREADS + tid;
+            if (t < ntgt) {
+                const int64_t i = act ? (int64_t)act[t] : t;
+                const double a = (tgt[i] - cc[0]) * scale, b = (tgt[Np + i] - cc[1]) * scale,
+                             d = (tgt[2 * Np + i] - cc[2]) * scale;
+                ok &= (a * a + b * b + d * d <= (double)EXP_R2) ? 1 : 0;   // false for NaN
+            }
+        }
+        if (__syncthreads_and(ok)) {
+            tile_packed_exp<KIND, THREADS, R>(buf, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part);
+            return;
+        }
+    }
+    tile_packed_diff<KIND, THREADS, R>(buf, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, part);
 }
 
 }  // namespace ssm

@@ -204,7 +204,7 @@ def test_coupled3d_fp32c_full_horizon_tolerances(S):
     assert np.max(np.abs(var_g - var_o)) < 1e-5
 
 
-@pytest.mark.parametrize("shape", [(1, 128, 4), (1, 256, 8), (1, 128, 8), (0, 256, 2), (0, 128, 8)])
+@pytest.mark.parametrize("shape", [(1, 128, 4), (1, 256, 8), (1, 128, 8), (2, 128, 4), (2, 256, 8), (0, 256, 2), (0, 128, 8)])
 def test_coupled3d_fp32c_every_launch_shape(S, shape):
     """Packed and scalar FP32 pair kernels of each compiled shape give the oracle's
     result within FP32-compensated accuracy (N = 1000: ragged tiles and chunks)."""
@@ -212,7 +212,7 @@ def test_coupled3d_fp32c_every_launch_shape(S, shape):
     s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=11, precision=S.SSM_FP32C)
     s.set_plan(0, *shape)
     s.set_plan(1, *shape)
-    assert s.plan(0)["packed"] == shape[0] and s.plan(0)["targets_per_thread"] == shape[2]
+    assert s.plan(0)["form"] == shape[0] and s.plan(0)["targets_per_thread"] == shape[2]
     s.run_steps(K)
     x, _ = s.get_state()
     s.close()
