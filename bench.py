@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batched", type=int, default=1, help="also time the 64-ensemble batched form (1/0)")
+    p.add_argument("--o-n", type=int, default=1, help="also time the O(N) kernels at N=2^26 against HBM (1/0)")
+    p.add_argument("--profile-o-n", type=int, default=0, metavar="LOG2N",
+                   help="profiling driver: 4 OU steps (d=3) at N = 2^LOG2N in the form of --precision, and exit")
     p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
@@ -77,6 +80,19 @@ def profile_kernels(args):
     s.step()
     s.pair_pass(0)
     s.pair_pass(1)
+    s.sync()
+    s.close()
+
+
+def profile_o_n(args):
+    """Small, self-terminating case for ncu: four OU steps of the O(N) kernels."""
+    from paper_2105_09688_gb300 import build as B
+    B.build()
+    import paper_2105_09688_gb300 as S
+    prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
+    s = S.SSM(d=ON_D, N=1 << args.profile_o_n, h=2.0 ** -6, T=1.0, coef=S.SSM_COEF_OU, seed=7, precision=prec,
+              coef_params=(-1.0, 0.5, 0.5), x0_mean=1.0, x0_std=0.5)
+    s.run_steps(4)
     s.sync()
     s.close()
 
@@ -217,6 +233,54 @@ def bench_batched(torch, S, stream):
     return res
 
 
+ON_LOG2N, ON_D = 26, 3
+ON_BYTES_PER_PARTICLE_STEP = 4 * 8 * ON_D   # implicit step: read X, write Y; step 2: read Y, write X (FP64)
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU type (generated file), else the
+    fallback figure; returns (GB/s, basis)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return 6800.0, "fallback"
+
+
+def bench_o_n(torch, S, stream, steps=5, warmup=3):
+    """The O(N) kernels against the HBM roofline: the OU coefficient set (implicit
+    step and explicit step are both per-particle, with grid-wide mean reductions),
+    d = 3, N = 2^26 (state 1.6 GB per array, far beyond L2), FP64 and FP32C forms.
+    Algorithmic bytes per particle-step: X read and Y written by the implicit step,
+    Y read and X written by step 2 (FP64 SoA)."""
+    peak, basis = hbm_peak_gbs()
+    N = 1 << ON_LOG2N
+    out = {"workload": "OU d=3 N=2^26 h=2^-6 (k_ou_implicit + k_euler per step)",
+           "bytes_per_particle_step": ON_BYTES_PER_PARTICLE_STEP, "peak_gbs": peak, "peak_basis": basis}
+    for name, prec in (("fp64", S.SSM_FP64), ("fp32c", S.SSM_FP32C)):
+        try:
+            s = S.SSM(d=ON_D, N=N, h=2.0 ** -6, T=1.0, coef=S.SSM_COEF_OU, seed=7, stream=stream, precision=prec,
+                      coef_params=(-1.0, 0.5, 0.5), x0_mean=1.0, x0_std=0.5)
+        except S.SSMError as e:
+            out[name] = {"error": str(e)}
+            continue
+        s.run_steps(warmup)
+        s.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        s.run_steps(steps)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1e3 / steps
+        gbs = N * ON_BYTES_PER_PARTICLE_STEP / dt / 1e9
+        out[name] = {"particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3, "achieved_gbs": gbs, "frac": gbs / peak}
+        s.close()
+    return out
+
+
 def aggregate_replicas(torch, world, local_seconds, local_units, device):
     """Whole-job throughput of independent replicas: every rank's units over the
     slowest rank's time (all-reduce MAX of the time; ranks hold equal work)."""
@@ -246,6 +310,9 @@ def main():
     world, rank, local = dist_setup()
     if args.profile_kernels:
         profile_kernels(args)
+        return
+    if args.profile_o_n:
+        profile_o_n(args)
         return
     import torch
     if world > 1:
@@ -388,6 +455,7 @@ def main():
         p.close()
 
     batched = bench_batched(torch, S, stream) if args.batched else None
+    o_n = bench_o_n(torch, S, stream) if args.o_n else None
 
     kmax = 12
     launches_per_step = 1 + 2 * kmax + 1 + 1 + 1 + 1 + (1 if form.startswith("learned") else 0)
@@ -405,6 +473,7 @@ def main():
             "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
             "plain_fp64": fp64,
             "batched_form": batched,
+            "o_n_kernels": o_n,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -64,12 +64,16 @@ typedef enum {
  *  SSM_COEF_COUPLED1D (d = 1): the three formulas of SSM_COEF_COUPLED3D at d = 1. */
 typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2, SSM_COEF_COUPLED1D = 3 } ssm_coef;
 
-/* Arithmetic of the O(N^2) pair sums.
+/* Arithmetic of a step.
  *  SSM_FP64: IEEE double throughout.
  *  SSM_FP32C: pair terms in FP32, summed in FP32 over blocks of 256 sources whose
  *      block sums are combined with error-free (two-sum) compensation and then in
- *      double; the Newton residual, the per-particle solves, the state and the
- *      moments stay in double.
+ *      double; the Newton residual, the per-particle solves and the state stay in
+ *      double.  Step 2 draws the same Philox words but evaluates the Box-Muller
+ *      transform in FP32 (|z error| < 5e-6) and forms the increment h b + sigma dW
+ *      in FP32 before adding it to the FP64 state; the moments are FP32 powers
+ *      summed in compensated FP32 per thread and in double across threads.
+ *      X_0 is drawn in FP64 in both forms.
  *  SSM_FP32C_LEARNED: SSM_FP32C with a learned initial guess for step 1
  *      (SSM_COEF_COUPLED3D only; load weights with ssm_ws_load). */
 typedef enum { SSM_FP64 = 0, SSM_FP32C = 1, SSM_FP32C_LEARNED = 2 } ssm_precision;
@@ -119,7 +123,8 @@ size_t ssm_workspace_bytes(int d, int64_t N, int coef, const ssm_opts *opts);
 /* Create a context for N particles in R^d on [0, T] with step h (§2.3: M = T/h
  * steps; h must divide T to 1e-12 relative).  Draws X_0 on the device from the
  * Philox4x32-10 stream of `seed` (stream 0).  Rejects with SSM_EINVAL: d not
- * supported by `coef` (CUBIC1D: 1, COUPLED3D: 3, OU: 1..3), N < 1 or N > 2^26,
+ * supported by `coef` (CUBIC1D: 1, COUPLED3D: 3, OU: 1..3), a precision the set
+ * has no form for (SSM_FP32C_LEARNED is COUPLED3D only), N < 1 or N > 2^26,
  * h <= 0, T <= 0, or h above the step-size bound of Theorem 2.3,
  * h <= 1/(1 + 2 L_v) when L_v > -1/2 (L_v = 1 for CUBIC1D, 1/16 for COUPLED3D,
  * rho for OU).  *out receives the context, or NULL on error. */
@@ -175,6 +180,16 @@ ssm_status ssm_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *o
 /* The d standard normals of particles 0..N-1 at counter (i, step, stream) that the
  * step uses (Box-Muller of Philox uniforms), out[N*d] on the host. */
 ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream, double *out);
+
+/* The same normals as the FP32C forms evaluate them (FP32 Box-Muller of the same
+ * Philox uniforms; |error| < 5e-6 against ssm_normals), out[N*d] on the host. */
+ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int stream, float *out);
+
+/* The binary64 -> binary32 (round to nearest even) and binary32 -> binary64
+ * conversions that the FP32C kernels perform with integer instructions, run on
+ * the host on the same source: out32[k] = (float)in[k], out64[k] = (double)out32[k]
+ * for k < n (host arrays).  For checking them against another implementation. */
+ssm_status ssm_convert_check(const double *in, int64_t n, float *out32, double *out64);
 
 /* Step 1 for SSM_COEF_CUBIC1D_GAUSS alone: y[k] = the real root of
  * h y^3 + (1 - h) y - x[k] = 0 (Lemma 4.1's F_h for v = x - x^3), 0 < h < 1/3. */

@@ -22,7 +22,7 @@ __all__ = [
     "SSM_FP32C_LEARNED", "SSM_STAGE_Y", "SSM_STAGE_B", "SSMError", "ssm_opts", "ssm_stats_t", "lib",
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
-    "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
+    "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_normals_fp32", "ssm_convert_check", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
     "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "load_ws",
     "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
     "ssm_ws_num_params",
@@ -85,6 +85,8 @@ _SIGS = {
     "ssm_status_str": (ctypes.c_char_p, [_i32]),
     "ssm_philox": (_i32, [_u64, _U32P, _i64, _U32P]),
     "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
+    "ssm_normals_fp32": (_i32, [_u64, _i32, _i64, _i64, _i32, ctypes.POINTER(ctypes.c_float)]),
+    "ssm_convert_check": (_i32, [_DP, _i64, ctypes.POINTER(ctypes.c_float), _DP]),
     "ssm_cardano": (_i32, [_DP, _i64, _dbl, _DP]),
     "ssm_pair_pass": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "ssm_autotune": (_i32, [_vp, _DP]),
@@ -381,6 +383,24 @@ def ssm_philox(seed, ctr):
 def ssm_normals(seed, d, N, step, stream):
     out = np.empty((int(N), int(d)))
     _check(lib().ssm_normals(int(seed), int(d), int(N), int(step), int(stream), _dp(out)), "ssm_normals")
+    return out
+
+
+def ssm_convert_check(values):
+    """The library's integer-pipe conversions run on the host: (float32 of each
+    value, float64 of that float32)."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    o32 = np.empty(v.size, dtype=np.float32)
+    o64 = np.empty(v.size, dtype=np.float64)
+    _check(lib().ssm_convert_check(_dp(v), v.size, o32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dp(o64)),
+           "ssm_convert_check")
+    return o32, o64
+
+
+def ssm_normals_fp32(seed, d, N, step, stream):
+    out = np.empty((int(N), int(d)), dtype=np.float32)
+    _check(lib().ssm_normals_fp32(int(seed), int(d), int(N), int(step), int(stream),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "ssm_normals_fp32")
     return out
 
 

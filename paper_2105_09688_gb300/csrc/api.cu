@@ -27,6 +27,8 @@ cudaError_t launch_soa_to_aos(const double *s, double *a, int d, int64_t N, int6
 cudaError_t launch_stage_b(ssm_ctx *c, double bscale);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_normals(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, double *out, cudaStream_t st);
+cudaError_t launch_normals32(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, float *out,
+                             cudaStream_t st);
 cudaError_t ws_forward_start(ssm_ctx *c);
 }  // namespace ssm
 
@@ -194,7 +196,6 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
         Lv = 1.0 / 16.0;
     } else if (coef == SSM_COEF_OU) {
         if (d < 1 || d > 3) return SSM_EINVAL;
-        if (o.precision != SSM_FP64) return SSM_EINVAL;
         Lv = o.coef_params[0];
     } else {
         return SSM_EINVAL;
@@ -527,6 +528,26 @@ ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream
     cudaError_t e = cudaMalloc((void **)&dz, sizeof(double) * d * N);
     if (e == cudaSuccess) e = launch_normals(seed, d, N, (uint32_t)step, (uint32_t)stream, dz, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, dz, sizeof(double) * d * N, cudaMemcpyDeviceToHost);
+    cudaFree(dz);
+    return cuda_status(e);
+}
+
+ssm_status ssm_convert_check(const double *in, int64_t n, float *out32, double *out64) {
+    if (n < 0 || (n > 0 && (!in || !out32 || !out64))) return SSM_EINVAL;
+    for (int64_t k = 0; k < n; ++k) {
+        out32[k] = f64_to_f32(in[k]);
+        out64[k] = f32_to_f64(out32[k]);
+    }
+    return SSM_OK;
+}
+
+ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int stream, float *out) {
+    if (!out || d < 1 || d > 3 || N < 0 || N > N_MAX || step < 0 || step > 0xffffffffll || stream < 0) return SSM_EINVAL;
+    if (N == 0) return SSM_OK;
+    float *dz = nullptr;
+    cudaError_t e = cudaMalloc((void **)&dz, sizeof(float) * d * N);
+    if (e == cudaSuccess) e = launch_normals32(seed, d, N, (uint32_t)step, (uint32_t)stream, dz, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dz, sizeof(float) * d * N, cudaMemcpyDeviceToHost);
     cudaFree(dz);
     return cuda_status(e);
 }

@@ -46,7 +46,7 @@ constexpr int SEGT = 256;    // threads (and particles per segment) of the O(N) 
 constexpr int64_t NMAX_ENS = (int64_t)1 << 24;
 
 struct BEns {                // one ensemble, in device memory
-    int d, active, fine_r, chunks;
+    int d, active, fine_r, chunks, fp32, pad_;
     int64_t N, Np, M, chunk_len, seg0, nseg;
     long long n;
     uint64_t seed;
@@ -264,9 +264,11 @@ kb_update(BEns *ens, int n_ens, BGlobal *g, int kmax, int fp32, cudaGraphConditi
 }
 
 // Step 2 per 256-particle segment, with that segment's moment partial sums.
+// Step 2 of one particle; the FP32C form draws dW from the FP32 transform and forms
+// the increment in FP32, exactly as the single-context kernel does.
 template <int D>
 __device__ __forceinline__ void euler_segment(const BEns &E, int64_t i, double (&m)[12]) {
-    double yv[D], b[D], dw[D];
+    double yv[D], b[D], inc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         yv[c] = E.y[c * E.Np + i];
@@ -274,10 +276,21 @@ __device__ __forceinline__ void euler_segment(const BEns &E, int64_t i, double (
         for (int k = 0; k < E.chunks; ++k) s += E.part[((int64_t)k * D + c) * E.Np + i];
         b[c] = s * E.bscale;
     }
-    brownian<D>(E.seed, i, E.n, E.sqrt_h, E.fine_r, E.sqrt_hf, dw);
+    if (E.fp32) {
+        float dw[D];
+        brownian32<D>(E.seed, i, E.n, (float)E.sqrt_h, E.fine_r, (float)E.sqrt_hf, dw);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            inc[c] = (double)fmaf(sigma_of32(SSM_COEF_COUPLED3D, (float)yv[c], 0.0f), dw[c], (float)E.h * (float)b[c]);
+    } else {
+        double dw[D];
+        brownian<D>(E.seed, i, E.n, E.sqrt_h, E.fine_r, E.sqrt_hf, dw);
+#pragma unroll
+        for (int c = 0; c < D; ++c) inc[c] = E.h * b[c] + sigma_of(SSM_COEF_COUPLED3D, yv[c], 0.0) * dw[c];
+    }
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-        const double xn = yv[c] + E.h * b[c] + sigma_of(SSM_COEF_COUPLED3D, yv[c], 0.0) * dw[c];
+        const double xn = yv[c] + inc[c];
         E.x[c * E.Np + i] = xn;
         const double x2 = xn * xn;
         m[0 * 3 + c] += xn;
@@ -597,6 +610,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         const ssm_ens_desc &D = desc[k];
         BEns &E = b->h_ens[k];
         E.d = D.d;
+        E.fp32 = b->f32 ? 1 : 0;
         E.N = D.N;
         E.Np = (D.N + 127) / 128 * 128;
         E.M = (int64_t)nearbyint(D.T / D.h);

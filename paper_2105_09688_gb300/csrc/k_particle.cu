@@ -130,30 +130,38 @@ __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, 
         y[i] = cardano_root(x[i], h);
 }
 
-// Step 1, SSM_COEF_OU (v = rho x): Y = X / (1 - h rho) (Remark 4.3), and the mean
-// of Y that step 2's b = lambda * mean needs.
-template <int D>
+// Step 1, SSM_COEF_OU (v = rho x): Y = X / (1 - h rho) (Remark 4.3), taken as a
+// product with the reciprocal (FP64 division costs many FP64-pipe instructions,
+// and that pipe runs at 1/64 of the FP32 rate here), and the mean of Y that
+// step 2's b = lambda * mean needs -- summed in compensated FP32 per thread in the
+// FP32C form, in FP64 otherwise; blocks combine in FP64.
+template <int D, bool F32>
 __global__ void __launch_bounds__(EUL_THREADS)
-k_ou_implicit(const double *x, double *y, int64_t N, int64_t Np, double inv, double *mpart, unsigned *ticket,
-              double *ymean) {
+k_ou_implicit(const double *__restrict__ x, double *__restrict__ y, int64_t N, int64_t Np, double rinv, double *mpart,
+              unsigned *ticket, double *ymean) {
     double m[D];
+    float mh[D], ml[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) m[c] = 0.0;
+    for (int c = 0; c < D; ++c) { m[c] = 0.0; mh[c] = 0.0f; ml[c] = 0.0f; }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double v = x[c * Np + i] / inv;
+            const double v = x[c * Np + i] * rinv;
             y[c * Np + i] = v;
-            m[c] += v;
+            if (F32) two_sum_acc(mh[c], ml[c], f64_to_f32(v));
+            else m[c] += v;
         }
+    if (F32)
+#pragma unroll
+        for (int c = 0; c < D; ++c) m[c] = (double)mh[c] + (double)ml[c];
     __shared__ double bsum[D];
     block_sum<D, EUL_THREADS>(m, bsum);
     __syncthreads();
     if (threadIdx.x < D) mpart[(int64_t)blockIdx.x * D + threadIdx.x] = bsum[threadIdx.x];
     if (last_block(ticket) && threadIdx.x < D) {
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&mpart[(int64_t)b * D + threadIdx.x]);
-        ymean[threadIdx.x] = s / (double)N;
+        double sm = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) sm += __ldcg(&mpart[(int64_t)b * D + threadIdx.x]);
+        ymean[threadIdx.x] = sm / (double)N;
     }
 }
 
@@ -282,7 +290,10 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // step's own grid (fine_r = 1) or summed over fine_r increments of the finer
 // grid, so that runs at different h share one Brownian path.
 // ---------------------------------------------------------------------------
-template <int D>
+// FP32C form (F32): dW from the FP32 transform, the increment h b + sigma dW in FP32
+// added to the FP64 state with one FP64 add, and the moments from FP32 powers in
+// compensated FP32 per thread (FP64 across threads and blocks).  FP64 form: all FP64.
+template <int D, bool F32>
 __global__ void __launch_bounds__(EUL_THREADS)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
         double bscale, int coef, double lam, double eta, const double *__restrict__ ymean, int64_t N, int64_t Np,
@@ -290,29 +301,53 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
         unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
     double m[4 * D];
+    float mh[4 * D], ml[4 * D];
 #pragma unroll
-    for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
+    for (int k = 0; k < 4 * D; ++k) { m[k] = 0.0; mh[k] = 0.0f; ml[k] = 0.0f; }
+    const bool ou = coef == SSM_COEF_OU;
+    float hb_ou[D];   // h b of OU (the same for every particle)
+#pragma unroll
+    for (int c = 0; c < D; ++c) hb_ou[c] = ou ? (float)(h * lam * ymean[c]) : 0.0f;
+    const float hf = (float)h, etaf = (float)eta;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double yv[D], b[D], dw[D];
+        double yv[D], b[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             yv[c] = y[c * Np + i];
-            if (coef == SSM_COEF_OU) {
-                b[c] = lam * ymean[c];
+            b[c] = 0.0;
+            if (ou) {
+                if (!F32) b[c] = lam * ymean[c];
             } else {
-                double s = 0.0;
-                for (int k = 0; k < chunks; ++k) s += part[((int64_t)k * D + c) * Np + i];
-                b[c] = s * bscale;
+                double sm = 0.0;
+                for (int k = 0; k < chunks; ++k) sm += part[((int64_t)k * D + c) * Np + i];
+                b[c] = sm * bscale;
             }
         }
-        brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
+        if (F32) {
+            float dw[D];
+            brownian32<D>(seed, i, n, (float)sqrt_h, fine_r, (float)sqrt_hf, dw);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const double xn = yv[c] + h * b[c] + sigma_of(coef, yv[c], eta) * dw[c];
-            x[c * Np + i] = xn;
-            add_powers<D>(m, c, xn);
+            for (int c = 0; c < D; ++c) {
+                const float yf = f64_to_f32(yv[c]);
+                const float hb = ou ? hb_ou[c] : hf * f64_to_f32(b[c]);
+                const float inc = fmaf(sigma_of32(coef, yf, etaf), dw[c], hb);
+                x[c * Np + i] = yv[c] + f32_to_f64(inc);
+                add_powers32<D>(mh, ml, c, yf + inc);
+            }
+        } else {
+            double dw[D];
+            brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const double xn = yv[c] + h * b[c] + sigma_of(coef, yv[c], eta) * dw[c];
+                x[c * Np + i] = xn;
+                add_powers<D>(m, c, xn);
+            }
         }
     }
+    if (F32)
+#pragma unroll
+        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] + (double)ml[k];
     moments_epilogue<D>(m, N, mpart, ticket, mom, err);
 }
 
@@ -378,6 +413,16 @@ __global__ void k_normals(uint64_t seed, int64_t N, uint32_t step, uint32_t stre
     }
 }
 
+template <int D>
+__global__ void k_normals32(uint64_t seed, int64_t N, uint32_t step, uint32_t stream, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        float z[3];
+        normals32<D>(seed, (uint32_t)i, step, stream, z);
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[i * D + c] = z[c];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers (enqueue only).
 // ---------------------------------------------------------------------------
@@ -421,10 +466,17 @@ cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cuda
 }
 
 cudaError_t launch_ou_implicit(ssm_ctx *c) {
-    const double inv = 1.0 - c->h * c->opt.coef_params[0];
-    if (c->d == 1) k_ou_implicit<1><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
-    else if (c->d == 2) k_ou_implicit<2><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
-    else k_ou_implicit<3><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, inv, c->mpart, c->ticket, c->ymean);
+    const double rinv = 1.0 / (1.0 - c->h * c->opt.coef_params[0]);
+    const bool f32 = c->prec != SSM_FP64;
+#define SSM_OU(D) \
+    if (f32) k_ou_implicit<D, true><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, rinv, c->mpart, \
+                                                                          c->ticket, c->ymean); \
+    else k_ou_implicit<D, false><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, rinv, c->mpart, \
+                                                                       c->ticket, c->ymean);
+    if (c->d == 1) { SSM_OU(1) }
+    else if (c->d == 2) { SSM_OU(2) }
+    else { SSM_OU(3) }
+#undef SSM_OU
     return cudaGetLastError();
 }
 
@@ -459,11 +511,13 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const double sqrt_hf = c->opt.fine_log2 > 0 ? sqrt(c->T / (double)(1ll << c->opt.fine_log2)) : 0.0;
     const int chunks = c->plan_drift.chunks;
     const double lam = c->opt.coef_params[1], eta = c->opt.coef_params[2];
-#define SSM_EUL(D) k_euler<D><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, c->coef, lam, eta, \
-        c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, c->mom, c->err, c->counters)
-    if (c->d == 1) SSM_EUL(1);
-    else if (c->d == 2) SSM_EUL(2);
-    else SSM_EUL(3);
+    const bool f32 = c->prec != SSM_FP64;
+#define SSM_EUL(D, F) k_euler<D, F><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, c->coef, \
+        lam, eta, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, \
+        c->mom, c->err, c->counters)
+    if (c->d == 1) { if (f32) SSM_EUL(1, true); else SSM_EUL(1, false); }
+    else if (c->d == 2) { if (f32) SSM_EUL(2, true); else SSM_EUL(2, false); }
+    else { if (f32) SSM_EUL(3, true); else SSM_EUL(3, false); }
 #undef SSM_EUL
     k_advance<<<1, 1, 0, c->st>>>(c->dstep, c->counters, c->N);
     return cudaGetLastError();
@@ -495,6 +549,14 @@ cudaError_t launch_normals(uint64_t seed, int d, int64_t N, uint32_t step, uint3
     if (d == 1) k_normals<1><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
     else if (d == 2) k_normals<2><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
     else k_normals<3><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normals32(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, float *out,
+                             cudaStream_t st) {
+    if (d == 1) k_normals32<1><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    else if (d == 2) k_normals32<2><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
+    else k_normals32<3><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
     return cudaGetLastError();
 }
 

@@ -138,11 +138,48 @@ __device__ __forceinline__ void brownian(uint64_t seed, int64_t i, long long n, 
     }
 }
 
+// The same increments in FP32 (FP32C forms).
+template <int D>
+__device__ __forceinline__ void brownian32(uint64_t seed, int64_t i, long long n, float sqrt_h, int fine_r,
+                                           float sqrt_hf, float *dw) {
+    if (fine_r <= 1) {
+        float z[3];
+        normals32<D>(seed, (uint32_t)i, (uint32_t)n, 1u, z);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dw[c] = sqrt_h * z[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dw[c] = 0.0f;
+        for (int r = 0; r < fine_r; ++r) {
+            float z[3];
+            normals32<D>(seed, (uint32_t)i, (uint32_t)(n * fine_r + r), 1u, z);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dw[c] = fmaf(sqrt_hf, z[c], dw[c]);
+        }
+    }
+}
+
 // Diffusion coefficient of each coefficient set, evaluated at Y (step 2).
 __device__ __forceinline__ double sigma_of(int coef, double y, double eta) {
     if (coef == SSM_COEF_CUBIC1D_GAUSS) return 0.4 * y + 0.1;
     if (coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D) return 0.3 * y + 0.2;
     return eta;
+}
+
+__device__ __forceinline__ float sigma_of32(int coef, float y, float eta) {
+    if (coef == SSM_COEF_CUBIC1D_GAUSS) return fmaf(0.4f, y, 0.1f);
+    if (coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D) return fmaf(0.3f, y, 0.2f);
+    return eta;
+}
+
+// Powers 1..4 of v accumulated in compensated FP32 (hi + lo per moment).
+template <int D>
+__device__ __forceinline__ void add_powers32(float (&hi)[4 * D], float (&lo)[4 * D], int c, float v) {
+    const float v2 = v * v;
+    two_sum_acc(hi[0 * D + c], lo[0 * D + c], v);
+    two_sum_acc(hi[1 * D + c], lo[1 * D + c], v2);
+    two_sum_acc(hi[2 * D + c], lo[2 * D + c], v2 * v);
+    two_sum_acc(hi[3 * D + c], lo[3 * D + c], v2 * v2);
 }
 
 template <int D>

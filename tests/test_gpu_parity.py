@@ -207,18 +207,29 @@ def test_coupled3d_fp32c_full_horizon_tolerances(S):
 @pytest.mark.parametrize("shape", [(1, 128, 4), (1, 256, 8), (1, 128, 8), (2, 128, 4), (2, 256, 8), (0, 256, 2), (0, 128, 8)])
 def test_coupled3d_fp32c_every_launch_shape(S, shape):
     """Packed and scalar FP32 pair kernels of each compiled shape give the oracle's
-    result within FP32-compensated accuracy (N = 1000: ragged tiles and chunks)."""
+    result within FP32-compensated accuracy (N = 1000: ragged tiles and chunks):
+    the first step's Y (step 1) and b (step 2) element by element, then the state
+    after 8 steps, which also carries the FP32 normals of step 2 (|dz| < 5e-6, so
+    |dx| < sigma sqrt(h) 5e-6 <= 1.2 * 2^-4 * 5e-6 = 3.8e-7 per step)."""
     N, h, K = 1000, 2.0 ** -8, 8
     s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=11, precision=S.SSM_FP32C)
     s.set_plan(0, *shape)
     s.set_plan(1, *shape)
     assert s.plan(0)["form"] == shape[0] and s.plan(0)["targets_per_thread"] == shape[2]
-    s.run_steps(K)
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=11)
+    x0, _ = s.get_state()
+    s.step()
+    y = s.get_stage(S.SSM_STAGE_Y)
+    b = s.get_stage(S.SSM_STAGE_B)
+    yo, it, bad = O.implicit_step(P, x0)
+    assert bad == 0 and relerr(y, yo) < 2e-9
+    bo = np.stack([O.drift_one(P, y, i) for i in range(N)])
+    assert np.max(np.abs(b - bo)) < 5e-7
+    s.run_steps(K - 1)
     x, _ = s.get_state()
     s.close()
-    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=11)
     xo = O.run(P, O.init_x0(P), 0, K)
-    assert np.max(np.abs(x - xo)) < 1e-7
+    assert np.max(np.abs(x - xo)) < K * 3.8e-7
 
 
 def test_autotune_changes_shape_not_results(S):
@@ -249,7 +260,7 @@ def test_coupled3d_full_size_sampled_fp32c(S):
     N, h = 1 << 18, 2.0 ** -8
     s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2, precision=S.SSM_FP32C)
     P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=2)
-    _sampled_step_check(S, s, P, 24, 2e-9, 2e-7)
+    _sampled_step_check(S, s, P, 24, 2e-9, 6e-7)   # x: + sigma sqrt(h) |dz| < 3.8e-7 from the FP32 normals
     st = s.stats()
     assert sum(st["hist"]) == N
     s.close()
