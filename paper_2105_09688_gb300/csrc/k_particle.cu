@@ -293,61 +293,84 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // FP32C form (F32): dW from the FP32 transform, the increment h b + sigma dW in FP32
 // added to the FP64 state with one FP64 add, and the moments from FP32 powers in
 // compensated FP32 per thread (FP64 across threads and blocks).  FP64 form: all FP64.
+// Compiled for RED_BLOCKS / 152 = 4 resident blocks per SM, so its fixed grid is one wave.
 template <int D, bool F32>
-__global__ void __launch_bounds__(EUL_THREADS)
+__global__ void __launch_bounds__(EUL_THREADS, 4)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
         double bscale, int coef, double lam, double eta, const double *__restrict__ ymean, int64_t N, int64_t Np,
         double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep, double *mpart,
         unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
-    double m[4 * D];
-    float mh[4 * D], ml[4 * D];
-#pragma unroll
-    for (int k = 0; k < 4 * D; ++k) { m[k] = 0.0; mh[k] = 0.0f; ml[k] = 0.0f; }
     const bool ou = coef == SSM_COEF_OU;
-    float hb_ou[D];   // h b of OU (the same for every particle)
+    // b of particle i (OU: lambda mean(Y), the same for all particles)
+    auto drift = [&](int64_t i, int c) -> double {
+        if (ou) return lam * ymean[c];
+        double sm = 0.0;
+        for (int k = 0; k < chunks; ++k) sm += part[((int64_t)k * D + c) * Np + i];
+        return sm * bscale;
+    };
+    double m[4 * D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) hb_ou[c] = ou ? (float)(h * lam * ymean[c]) : 0.0f;
-    const float hf = (float)h, etaf = (float)eta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double yv[D], b[D];
+    for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (F32) {
+        float hb_ou[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            yv[c] = y[c * Np + i];
-            b[c] = 0.0;
-            if (ou) {
-                if (!F32) b[c] = lam * ymean[c];
-            } else {
-                double sm = 0.0;
-                for (int k = 0; k < chunks; ++k) sm += part[((int64_t)k * D + c) * Np + i];
-                b[c] = sm * bscale;
+        for (int c = 0; c < D; ++c) hb_ou[c] = ou ? (float)(h * lam * ymean[c]) : 0.0f;
+        const float hf = (float)h, etaf = (float)eta, sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
+        // X' = Y + inc for particle i; returns the FP32 powers 1..4 of X' (4 D values).
+        // The loads are issued before the Philox and Box-Muller arithmetic they overlap.
+        auto advance = [&](int64_t i, float (&p)[4 * D]) {
+            double yv[D];
+            float hb[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                yv[c] = y[c * Np + i];
+                hb[c] = ou ? hb_ou[c] : hf * f64_to_f32(drift(i, c));
             }
-        }
-        if (F32) {
             float dw[D];
-            brownian32<D>(seed, i, n, (float)sqrt_h, fine_r, (float)sqrt_hf, dw);
+            brownian32<D>(seed, i, n, sqh, fine_r, sqhf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 const float yf = f64_to_f32(yv[c]);
-                const float hb = ou ? hb_ou[c] : hf * f64_to_f32(b[c]);
-                const float inc = fmaf(sigma_of32(coef, yf, etaf), dw[c], hb);
+                const float inc = fmaf(sigma_of32(coef, yf, etaf), dw[c], hb[c]);
                 x[c * Np + i] = yv[c] + f32_to_f64(inc);
-                add_powers32<D>(mh, ml, c, yf + inc);
+                const float v = yf + inc, v2 = v * v;
+                p[0 * D + c] = v;
+                p[1 * D + c] = v2;
+                p[2 * D + c] = v2 * v;
+                p[3 * D + c] = v2 * v2;
             }
-        } else {
+        };
+        float mh[4 * D], ml[4 * D];
+#pragma unroll
+        for (int k = 0; k < 4 * D; ++k) { mh[k] = 0.0f; ml[k] = 0.0f; }
+        // two particles per iteration: their powers are added before the compensated sum
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += 2 * stride) {
+            float p[4 * D], q[4 * D];
+            advance(i, p);
+            if (i + stride < N) advance(i + stride, q);
+            else
+#pragma unroll
+                for (int k = 0; k < 4 * D; ++k) q[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4 * D; ++k) two_sum_acc(mh[k], ml[k], p[k] + q[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] + (double)ml[k];
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
             double dw[D];
             brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const double xn = yv[c] + h * b[c] + sigma_of(coef, yv[c], eta) * dw[c];
+                const double yv = y[c * Np + i];
+                const double xn = yv + h * drift(i, c) + sigma_of(coef, yv, eta) * dw[c];
                 x[c * Np + i] = xn;
                 add_powers<D>(m, c, xn);
             }
         }
     }
-    if (F32)
-#pragma unroll
-        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] + (double)ml[k];
     moments_epilogue<D>(m, N, mpart, ticket, mom, err);
 }
 
