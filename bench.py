@@ -38,6 +38,28 @@ FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
 # operations): step 1: 1 + 3 x 2 (q) + 3 x 2 + 1 = 14; drift: 3 x 2 + 3 x 2 + 1 = 13.
 FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
 FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
+# DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 8> at
+# N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), valid only for the
+# kernel sources it was measured on (their SHA-256 below); otherwise the roofline's
+# traffic is null.
+MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 8, 1 << 18), "bytes": 13293312 + 2779392,
+                    "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu",
+                                "paper_2105_09688_gb300/csrc/ssm_device.cuh"),
+                    "sha256": "83792ea6f36f37c0218fea8679ca465e9b4c34e71c4bd2a20765e3df87f9d236"}
+
+
+def measured_traffic(kernel, kind, threads, rpt, n):
+    """The ncu DRAM bytes per launch of this kernel if they were measured on the
+    current sources, else None."""
+    import hashlib
+    m = MEASURED_TRAFFIC
+    if (kernel, kind, threads, rpt, n) != m["kernel"]:
+        return None
+    h = hashlib.sha256()
+    for f in m["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return m["bytes"] if h.hexdigest() == m["sha256"] else None
 METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
 
 
@@ -381,10 +403,13 @@ def main():
     sm_mhz = MAX_SM_MHZ
     peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / t_dom / 1e12
-    dom_form = plans["step1_pairs" if dom == 0 else "drift_pairs"]["form"]
+    dom_plan = plans["step1_pairs" if dom == 0 else "drift_pairs"]
+    dom_form = dom_plan["form"]
     executed = (FLOPS_PAIR_EXPANDED if dom_form == 2 else FLOPS_PAIR)[dom] * N_PART * N_PART / t_dom / 1e12
+    traffic = measured_traffic(("k_pair", "k_pair2", "k_pair2x")[dom_form], dom, dom_plan["threads"],
+                               dom_plan["targets_per_thread"], N_PART)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
                 "kernel": "%s<%s> (%s)" % (("k_pair", "k_pair2", "k_pair2x")[dom_form],
                                            "PK_NEWTON3" if dom == 0 else "PK_DRIFT3", FORM_NAMES[dom_form]),
                 "flops_per_pair": FLOPS_PAIR[dom],
