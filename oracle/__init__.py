@@ -17,6 +17,10 @@ COEF_CUBIC1D_GAUSS = 0
 COEF_COUPLED3D = 1
 COEF_OU = 2
 COEF_COUPLED1D = 3
+COEF_GL1 = 4          # §3.2, SSM version 1: v = -x^3, b = s^2/2 y + c mean, sigma = s y
+COEF_GL2 = 5          # §3.2, SSM version 2: v = -x^3 + c mean, b = s^2/2 y, sigma = s y
+COEF_POLY = 6         # §3.3: v = gamma x - x mean(x^2), b = mean, sigma = y
+COEF_CS = 7           # §3.4 Cucker-Smale, x = (V, X): v = (-V^3, 0), b = (1 + lambda (mean V - V), V)
 
 _c_int, _c_i64, _c_dbl, _c_u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
 
@@ -43,6 +47,7 @@ def lib():
             "orc_normals": (None, [_c_u64, _c_int, _c_i64, _c_i64, _c_int, dp]),
             "orc_brownian": (None, [P, _c_i64, _c_i64, dp]),
             "orc_cardano_cubic": (_c_dbl, [_c_dbl, _c_dbl]),
+            "orc_cardano_gl": (_c_dbl, [_c_dbl, _c_dbl]),
             "orc_implicit_one": (_c_int, [P, dp, _c_i64, dp]),
             "orc_implicit_point": (_c_int, [P, dp, dp, dp]),
             "orc_explicit_one": (None, [P, dp, _c_i64, _c_i64, dp]),
@@ -109,6 +114,11 @@ def brownian(P, i, n):
 
 def cardano(x, h):
     return float(lib().orc_cardano_cubic(float(x), float(h)))
+
+
+def cardano_gl(x, h):
+    """Root of y + h y^3 = x."""
+    return float(lib().orc_cardano_gl(float(x), float(h)))
 
 
 def init_x0(P):

@@ -33,6 +33,19 @@
  *   ORC_COEF_COUPLED1D: the same three formulas at d = 1.
  *   ORC_COEF_OU, any d (componentwise), §3.4.1 Eq. (stablity:OU):
  *     v(x) = rho x,  b(mu) = lambda * int z mu(dz),  sigma = eta.
+ *   The moment-interaction examples of §3 (each measure enters through a mean):
+ *   ORC_COEF_GL1, d = 1, §3.2 Eq. (MV-GL-SDE-veresion1), p = (sigma', c):
+ *     v(x) = -x^3,  b(y, mu) = sigma'^2/2 y + c int z mu(dz),  sigma(y) = sigma' y.
+ *   ORC_COEF_GL2, d = 1, §3.2 Eq. (MV-GL-SDE-veresion2), p = (sigma', c):
+ *     v(x, mu) = -x^3 + c int z mu(dz),  b(y) = sigma'^2/2 y,  sigma(y) = sigma' y.
+ *   ORC_COEF_POLY, d = 1, §3.3 Eq. (poly1), p = (gamma):
+ *     v(x, mu) = gamma x - x int z^2 mu(dz),  b(mu) = int z mu(dz),  sigma(y) = y.
+ *   ORC_COEF_CS, d = 2, x = (V, X), §3.4 (Cucker-Smale), p = (lambda, sigma'):
+ *     v = (-V^3, 0),  b(y, mu) = (1 + lambda int (z - V) mu^V(dz), V),
+ *     sigma(y, mu) = diag(sigma' int (z - V) mu^V(dz), 0).
+ *     The drift and diffusion integrals are taken with the sign of the paper's
+ *     particle system, (lambda/N) sum_j (V_j - V_i): the flocking towards the mean
+ *     that the section describes.
  *
  * The implicit step is solved as follows.
  *   CUBIC1D_GAUSS: h y^3 + (1 - h) y - x = 0 has exactly one real root for
@@ -42,6 +55,9 @@
  *     the exact d x d Jacobian, Gaussian elimination with partial pivoting, step
  *     halving when the residual grows, start y = x.
  *   OU: y = x / (1 - h rho) (Remark 4.3 gives this closed form for v = a x).
+ *   GL1, GL2, the V part of CS: y + h y^3 = x (+ h c mean(X) for GL2), one real
+ *     root for every h > 0, by the same Cardano form and Newton correction.
+ *   POLY: the equation is linear in y: y = x / (1 - h gamma + h mean(X^2)).
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), key = (seed mod 2^32, seed >> 32),
@@ -153,12 +169,41 @@ void orc_brownian(const orc_problem *P, int64_t i, int64_t n, double *dw)
 /* Coefficients                                                              */
 /* ------------------------------------------------------------------------ */
 
-/* b(y_i, mu^Y) for the pairwise sets; y is the particle-major array of all
- * particles (the support of the empirical measure). */
+/* (1/N) sum_j y_{j,c}^k over all particles: a plain moment of the empirical measure. */
+static double mean_power(const orc_problem *P, const double *y, int c, int k)
+{
+    double s = 0.0;
+    for (int64_t j = 0; j < P->N; ++j) {
+        double v = y[(int64_t)P->d * j + c], p = v;
+        for (int e = 1; e < k; ++e) p *= v;
+        s += p;
+    }
+    return s / (double)P->N;
+}
+
+/* b(y_i, mu^Y); y is the particle-major array of all particles (the support of
+ * the empirical measure). */
 static void drift_b(const orc_problem *P, const double *y, const double *yi, double *b)
 {
     const int d = P->d;
     const int64_t N = P->N;
+    if (P->coef == ORC_COEF_GL1) {
+        b[0] = P->p[0] * P->p[0] / 2.0 * yi[0] + P->p[1] * mean_power(P, y, 0, 1);
+        return;
+    }
+    if (P->coef == ORC_COEF_GL2) {
+        b[0] = P->p[0] * P->p[0] / 2.0 * yi[0];
+        return;
+    }
+    if (P->coef == ORC_COEF_POLY) {
+        b[0] = mean_power(P, y, 0, 1);
+        return;
+    }
+    if (P->coef == ORC_COEF_CS) {
+        b[0] = 1.0 + P->p[0] * (mean_power(P, y, 0, 1) - yi[0]);
+        b[1] = yi[0];
+        return;
+    }
     if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
         double s = 0.0;
         for (int64_t j = 0; j < N; ++j) {
@@ -184,10 +229,18 @@ static void drift_b(const orc_problem *P, const double *y, const double *yi, dou
     }
 }
 
-static void diffusion_times_dw(const orc_problem *P, const double *yi, const double *dw, double *out)
+static void diffusion_times_dw(const orc_problem *P, const double *y, const double *yi, const double *dw,
+                               double *out)
 {
     const int d = P->d;
-    if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
+    if (P->coef == ORC_COEF_GL1 || P->coef == ORC_COEF_GL2) {
+        out[0] = P->p[0] * yi[0] * dw[0];
+    } else if (P->coef == ORC_COEF_POLY) {
+        out[0] = yi[0] * dw[0];
+    } else if (P->coef == ORC_COEF_CS) {
+        out[0] = P->p[1] * (mean_power(P, y, 0, 1) - yi[0]) * dw[0];
+        out[1] = 0.0;
+    } else if (P->coef == ORC_COEF_CUBIC1D_GAUSS) {
         out[0] = (0.4 * yi[0] + 0.1) * dw[0];
     } else if (P->coef == ORC_COEF_COUPLED3D || P->coef == ORC_COEF_COUPLED1D) {
         for (int c = 0; c < d; ++c) out[c] = (0.3 * yi[c] + 0.2) * dw[c];
@@ -288,10 +341,11 @@ static double norminf(int d, const double *v) {
  * y = u + w, u w = -p/3, u^3 + w^3 = -q, the root is written as
  * -q / (u^2 - u w + w^2) = -q / (u^2 + p/3 + w^2): a sum of positive terms, so it
  * loses no digits when q is small. */
-double orc_cardano_cubic(double x, double h)
+static double cardano_root(double x, double h, double a)
 {
+    /* h y^3 + a y - x = 0 with a > 0, h > 0 */
     if (x == 0.0) return 0.0;
-    double p = (1.0 - h) / h;
+    double p = a / h;
     double q = -x / h;
     double disc = (q / 2.0) * (q / 2.0) + (p / 3.0) * (p / 3.0) * (p / 3.0);
     double sq = sqrt(disc);
@@ -299,10 +353,15 @@ double orc_cardano_cubic(double x, double h)
     if (q > 0.0) u = -u;
     double w = -p / (3.0 * u);
     double y = -q / (u * u + p / 3.0 + w * w);
-    double f = h * y * y * y + (1.0 - h) * y - x;
-    double fp = 3.0 * h * y * y + (1.0 - h);
+    double f = h * y * y * y + a * y - x;
+    double fp = 3.0 * h * y * y + a;
     return y - f / fp;
 }
+
+double orc_cardano_cubic(double x, double h) { return cardano_root(x, h, 1.0 - h); }
+
+/* Root of y + h y^3 = x: step 1 for v = -x^3 (the GL and Cucker-Smale sets). */
+double orc_cardano_gl(double x, double h) { return cardano_root(x, h, 1.0); }
 
 /* The implicit map F_h of Lemma 4.1: the root c of c = xi + h v(c, mu^X) for an
  * arbitrary point xi, with mu^X the empirical measure of the array x.  Returns
@@ -317,6 +376,23 @@ int orc_implicit_point(const orc_problem *P, const double *x, const double *xi, 
     }
     if (P->coef == ORC_COEF_OU) {
         for (int c = 0; c < d; ++c) y_out[c] = xi[c] / (1.0 - P->h * P->p[0]);
+        return 0;
+    }
+    if (P->coef == ORC_COEF_GL1) {
+        y_out[0] = orc_cardano_gl(xi[0], P->h);
+        return 0;
+    }
+    if (P->coef == ORC_COEF_GL2) {
+        y_out[0] = orc_cardano_gl(xi[0] + P->h * P->p[1] * mean_power(P, x, 0, 1), P->h);
+        return 0;
+    }
+    if (P->coef == ORC_COEF_POLY) {
+        y_out[0] = xi[0] / (1.0 - P->h * P->p[0] + P->h * mean_power(P, x, 0, 2));
+        return 0;
+    }
+    if (P->coef == ORC_COEF_CS) {
+        y_out[0] = orc_cardano_gl(xi[0], P->h);
+        y_out[1] = xi[1];
         return 0;
     }
     /* coupled sets: damped Newton from y = x_i. */
@@ -361,7 +437,7 @@ void orc_explicit_one(const orc_problem *P, const double *y, int64_t i, int64_t 
     double b[3], dw[3], sdw[3];
     drift_b(P, y, yi, b);
     orc_brownian(P, i, n, dw);
-    diffusion_times_dw(P, yi, dw, sdw);
+    diffusion_times_dw(P, y, yi, dw, sdw);
     for (int c = 0; c < d; ++c) x_out[c] = yi[c] + P->h * b[c] + sdw[c];
 }
 

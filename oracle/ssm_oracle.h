@@ -14,7 +14,8 @@
 
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_COEF_CUBIC1D_GAUSS = 0, ORC_COEF_COUPLED3D = 1, ORC_COEF_OU = 2, ORC_COEF_COUPLED1D = 3 };
+enum { ORC_COEF_CUBIC1D_GAUSS = 0, ORC_COEF_COUPLED3D = 1, ORC_COEF_OU = 2, ORC_COEF_COUPLED1D = 3,
+       ORC_COEF_GL1 = 4, ORC_COEF_GL2 = 5, ORC_COEF_POLY = 6, ORC_COEF_CS = 7 };
 
 typedef struct {
     int d;            /* space dimension: 1 or 3 (OU: any) */
@@ -23,7 +24,7 @@ typedef struct {
     double h;         /* step size */
     double T;         /* horizon (used for the fine Brownian grid) */
     uint64_t seed;    /* Philox key */
-    double p[4];      /* OU: rho, lambda, eta */
+    double p[4];      /* OU: rho, lambda, eta; GL1/GL2: sigma', c; POLY: gamma; CS: lambda, sigma' */
     double x0_mean;   /* X_0 = x0_mean + x0_std * Z */
     double x0_std;
     int fine_log2;    /* 0: own grid; L > 0: Brownian path on the grid T 2^-L */
@@ -33,6 +34,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 void orc_normals(uint64_t seed, int d, int64_t i, int64_t step, int stream, double *z);
 void orc_brownian(const orc_problem *P, int64_t i, int64_t n, double *dw);
 double orc_cardano_cubic(double x, double h);
+double orc_cardano_gl(double x, double h);
 int orc_implicit_point(const orc_problem *P, const double *x, const double *xi, double *y_out);
 int orc_implicit_one(const orc_problem *P, const double *x, int64_t i, double *y_out);
 void orc_explicit_one(const orc_problem *P, const double *y, int64_t i, int64_t n, double *x_out);
