@@ -300,6 +300,27 @@ def bench_o_n(torch, S, stream, steps=5, warmup=3):
         gbs = N * ON_BYTES_PER_PARTICLE_STEP / dt / 1e9
         out[name] = {"particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3, "achieved_gbs": gbs, "frac": gbs / peak}
         s.close()
+    # the paper's moment-interaction examples, FP32C, same N (32 d bytes per particle-step)
+    models = {}
+    for name, d, coef, p, m0, s0 in (("gl1", 1, S.SSM_COEF_GL1, (1.5, 0.5), 1.0, 0.0),
+                                     ("gl2", 1, S.SSM_COEF_GL2, (1.5, 0.5), 1.0, 0.0),
+                                     ("poly", 1, S.SSM_COEF_POLY, (-1.0,), 1.0, 0.0),
+                                     ("cs", 2, S.SSM_COEF_CS, (2.0, 4.0), 1.0, 2.0 ** 0.5)):
+        s = S.SSM(d=d, N=N, h=2.0 ** -6, T=1.0, coef=coef, seed=7, stream=stream, precision=S.SSM_FP32C,
+                  coef_params=p, x0_mean=m0, x0_std=s0)
+        s.run_steps(warmup)
+        s.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        s.run_steps(steps)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1e3 / steps
+        gbs = N * 32 * d / dt / 1e9
+        models[name] = {"d": d, "particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3, "achieved_gbs": gbs,
+                        "frac": gbs / peak}
+        s.close()
+    out["fp32c_moment_models"] = models
     return out
 
 

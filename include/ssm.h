@@ -61,8 +61,21 @@ typedef enum {
  *  SSM_COEF_OU (any d, componentwise; §3.4.1 Eq. (stablity:OU)): v(x) = rho x,
  *      b(mu) = lambda int z mu(dz), sigma = eta, with (rho, lambda, eta) taken
  *      from ssm_opts.coef_params[0..2].
- *  SSM_COEF_COUPLED1D (d = 1): the three formulas of SSM_COEF_COUPLED3D at d = 1. */
-typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2, SSM_COEF_COUPLED1D = 3 } ssm_coef;
+ *  SSM_COEF_COUPLED1D (d = 1): the three formulas of SSM_COEF_COUPLED3D at d = 1.
+ * The paper's examples whose measure enters through means (step 1 per particle,
+ * no pair sums; the parameters come from ssm_opts.coef_params):
+ *  SSM_COEF_GL1 (d = 1; §3.2 Eq. (MV-GL-SDE-veresion1)), params (s, c): v(x) = -x^3,
+ *      b(y, mu) = s^2/2 y + c int z mu(dz), sigma(y) = s y.  Step 1: y + h y^3 = x.
+ *  SSM_COEF_GL2 (d = 1; §3.2 Eq. (MV-GL-SDE-veresion2)), params (s, c):
+ *      v(x, mu) = -x^3 + c int z mu(dz), b(y) = s^2/2 y, sigma(y) = s y.
+ *  SSM_COEF_POLY (d = 1; §3.3 Eq. (poly1)), params (gamma): v(x, mu) = gamma x
+ *      - x int z^2 mu(dz), b(mu) = int z mu(dz), sigma(y) = y.  Step 1 is linear.
+ *  SSM_COEF_CS (d = 2, x = (V, X); §3.4 Cucker-Smale), params (lambda, s):
+ *      v = (-V^3, 0), b = (1 + lambda int (z - V) mu^V(dz), V),
+ *      sigma = diag(s int (z - V) mu^V(dz), 0) -- the sign of the paper's particle
+ *      system (a pull towards the mean velocity), not of its coefficient display. */
+typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2, SSM_COEF_COUPLED1D = 3,
+               SSM_COEF_GL1 = 4, SSM_COEF_GL2 = 5, SSM_COEF_POLY = 6, SSM_COEF_CS = 7 } ssm_coef;
 
 /* Arithmetic of a step.
  *  SSM_FP64: IEEE double throughout.
@@ -92,7 +105,7 @@ typedef struct {
                                at different h share one path (§3). */
     double x0_mean;         /* X_0 = x0_mean + x0_std Z, Z ~ N(0, I_d); default 0 */
     double x0_std;          /* default 1 */
-    double coef_params[4];  /* SSM_COEF_OU: rho, lambda, eta */
+    double coef_params[4];  /* OU: rho, lambda, eta; GL1/GL2: s, c; POLY: gamma; CS: lambda, s */
     void *stream;           /* cudaStream_t to enqueue on (borrowed); NULL = default stream */
     void *workspace;        /* optional caller-owned device memory, >= ssm_workspace_bytes(),
                                256-byte aligned; NULL = the context allocates */
@@ -123,11 +136,13 @@ size_t ssm_workspace_bytes(int d, int64_t N, int coef, const ssm_opts *opts);
 /* Create a context for N particles in R^d on [0, T] with step h (§2.3: M = T/h
  * steps; h must divide T to 1e-12 relative).  Draws X_0 on the device from the
  * Philox4x32-10 stream of `seed` (stream 0).  Rejects with SSM_EINVAL: d not
- * supported by `coef` (CUBIC1D: 1, COUPLED3D: 3, OU: 1..3), a precision the set
+ * supported by `coef` (CUBIC1D, COUPLED1D, GL1, GL2, POLY: 1; COUPLED3D: 3; CS: 2;
+ * OU: 1..3), a precision the set
  * has no form for (SSM_FP32C_LEARNED is COUPLED3D only), N < 1 or N > 2^26,
  * h <= 0, T <= 0, or h above the step-size bound of Theorem 2.3,
  * h <= 1/(1 + 2 L_v) when L_v > -1/2 (L_v = 1 for CUBIC1D, 1/16 for COUPLED3D,
- * rho for OU).  *out receives the context, or NULL on error. */
+ * rho for OU, 0 for GL1, GL2 and CS, gamma for POLY).  *out receives the context,
+ * or NULL on error. */
 ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t seed,
                       const ssm_opts *opts, ssm_ctx **out);
 

@@ -23,13 +23,14 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_normals_fp32", "ssm_convert_check", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "load_ws",
+    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "load_ws",
     "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
     "ssm_ws_num_params",
 ]
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
 SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU, SSM_COEF_COUPLED1D = 0, 1, 2, 3
+SSM_COEF_GL1, SSM_COEF_GL2, SSM_COEF_POLY, SSM_COEF_CS = 4, 5, 6, 7
 SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
 SSM_STAGE_Y, SSM_STAGE_B = 0, 1
 

@@ -16,7 +16,7 @@ namespace ssm {
 cudaError_t launch_init_x0(ssm_ctx *c);
 cudaError_t launch_moments(ssm_ctx *c);
 cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st);
-cudaError_t launch_ou_implicit(ssm_ctx *c);
+cudaError_t launch_mm_implicit(ssm_ctx *c);
 cudaError_t launch_newton_begin(ssm_ctx *c);
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32);
 cudaError_t launch_step_stats(ssm_ctx *c);
@@ -68,6 +68,11 @@ int kind_nc(int kind) {
     return kind == PK_NEWTON3 ? 4 : kind == PK_DRIFT3 ? 3 : kind == PK_NEWTON1 ? 2 : 1;
 }
 bool is_coupled(int coef) { return coef == SSM_COEF_COUPLED3D || coef == SSM_COEF_COUPLED1D; }
+// Sets whose measure enters only through means: no pair sums, a per-particle step 1.
+bool is_moment(int coef) {
+    return coef == SSM_COEF_OU || coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_POLY ||
+           coef == SSM_COEF_CS;
+}
 int newton_kind(int d) { return d == 1 ? PK_NEWTON1 : PK_NEWTON3; }
 int drift_kind(int coef) { return (coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM_COEF_COUPLED1D) ? PK_DRIFT1 : PK_DRIFT3; }
 
@@ -197,6 +202,15 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
     } else if (coef == SSM_COEF_OU) {
         if (d < 1 || d > 3) return SSM_EINVAL;
         Lv = o.coef_params[0];
+    } else if (coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2) {
+        if (d != 1) return SSM_EINVAL;
+        Lv = 0.0;                       // -x^3 (+ a measure term constant in x): one-sided constant 0
+    } else if (coef == SSM_COEF_POLY) {
+        if (d != 1) return SSM_EINVAL;
+        Lv = o.coef_params[0];          // gamma x - x mean(x^2): one-sided constant gamma - mean(x^2) <= gamma
+    } else if (coef == SSM_COEF_CS) {
+        if (d != 2) return SSM_EINVAL;
+        Lv = 0.0;                       // (-V^3, 0)
     } else {
         return SSM_EINVAL;
     }
@@ -250,8 +264,8 @@ cudaError_t enqueue_step(ssm_ctx *c) {
             return e;
         return launch_euler(c, bscale);
     }
-    if (c->coef == SSM_COEF_OU) {
-        if ((e = launch_ou_implicit(c)) != cudaSuccess) return e;
+    if (is_moment(c->coef)) {
+        if ((e = launch_mm_implicit(c)) != cudaSuccess) return e;
         return launch_euler(c, 0.0);
     }
     // SSM_COEF_COUPLED3D / SSM_COEF_COUPLED1D
@@ -555,7 +569,7 @@ ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int s
 ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
     if (!c || (which != 0 && which != 1)) return SSM_EINVAL;
     if (c->status != SSM_OK) return (ssm_status)c->status;
-    if (c->coef == SSM_COEF_OU || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
+    if (is_moment(c->coef) || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
     cudaError_t e;
     if (which == 0) {
@@ -577,7 +591,7 @@ ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
 ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
     if (!c) return SSM_EINVAL;
     if (c->status != SSM_OK) return (ssm_status)c->status;
-    if (c->coef == SSM_COEF_OU) return SSM_OK;
+    if (is_moment(c->coef)) return SSM_OK;
     const bool f32 = fp32_pairs(c);
     double scale, bscale;
     drift_scale(c->coef, f32, c->N, &scale, &bscale);
@@ -628,7 +642,7 @@ ssm_status ssm_get_plan(ssm_ctx *c, int which, int *out) {
 
 ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
     if (!c || !in || (which != 0 && which != 1)) return SSM_EINVAL;
-    if (c->coef == SSM_COEF_OU || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
+    if (is_moment(c->coef) || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
     const int kind = which == 0 ? newton_kind(c->d) : drift_kind(c->coef);
     int cand[32][3];

@@ -105,24 +105,44 @@ k_moments(const double *x, int64_t N, int64_t Np, double *mpart, unsigned *ticke
 }
 
 // ---------------------------------------------------------------------------
-// Step 1, SSM_COEF_CUBIC1D_GAUSS: the real root of h y^3 + (1-h) y - x = 0.
-// Depressed cubic y^3 + p y + q = 0, p = (1-h)/h > 0, q = -x/h: one real root.
-// With y = u + w, u w = -p/3 and u^3 + w^3 = -q, the root equals
-// -q / (u^2 + p/3 + w^2), a quotient of positive sums that keeps full relative
-// accuracy for small |x|.  One Newton correction follows.
+// Step 1 for a cubic drift: the real root of h y^3 + a y - x = 0, a > 0
+// (a = 1 - h for v = x - x^3, SSM_COEF_CUBIC1D_GAUSS; a = 1 for v = -x^3, the GL
+// and Cucker-Smale sets).  Depressed cubic y^3 + p y + q = 0, p = a/h > 0,
+// q = -x/h: one real root.  With y = u + w, u w = -p/3 and u^3 + w^3 = -q, the
+// root equals -q / (u^2 + p/3 + w^2), a quotient of positive sums that keeps full
+// relative accuracy for small |x|.  One Newton correction follows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double cardano_root(double x, double h) {
+__device__ __forceinline__ double cardano_root_a(double x, double h, double a) {
     if (x == 0.0) return 0.0;
-    const double p = (1.0 - h) / h, q = -x / h;
+    const double p = a / h, q = -x / h;
     const double p3 = p / 3.0;
     const double disc = 0.25 * q * q + p3 * p3 * p3;
     double u = cbrt(0.5 * fabs(q) + sqrt(disc));
     if (q > 0.0) u = -u;
     const double w = -p3 / u;
     const double y = -q / (u * u + p3 + w * w);
-    const double f = h * y * y * y + (1.0 - h) * y - x;
-    const double fp = 3.0 * h * y * y + (1.0 - h);
+    const double f = h * y * y * y + a * y - x;
+    const double fp = 3.0 * h * y * y + a;
     return y - f / fp;
+}
+__device__ __forceinline__ double cardano_root(double x, double h) { return cardano_root_a(x, h, 1.0 - h); }
+
+// The root of y + h y^3 = x for the FP32C forms: the same Cardano form in FP32
+// (relative error ~1e-6), then one Newton correction with the residual in FP64 and
+// the derivative in FP32, which leaves ~1e-13 relative (quadratic convergence, plus
+// the derivative's FP32 rounding times the first error), with five FP64 operations.
+__device__ __forceinline__ double cardano_gl32(double x, double h) {
+    const float xf = f64_to_f32(x), hf = (float)h;
+    const float p3 = 1.0f / (3.0f * hf), q = -xf / hf;
+    const float disc = 0.25f * q * q + p3 * p3 * p3;
+    float u = cbrtf(0.5f * fabsf(q) + sqrtf(disc));
+    if (q > 0.0f) u = -u;
+    const float w = -p3 / u;
+    const float y0 = -q / (u * u + p3 + w * w);
+    const double yd = f32_to_f64(y0);
+    const double f = fma(h * yd, yd * yd, yd) - x;
+    const float fp = fmaf(3.0f * hf * y0, y0, 1.0f);
+    return yd - f32_to_f64(f64_to_f32(f) / fp);
 }
 
 __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, int64_t n, double h) {
@@ -130,23 +150,38 @@ __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, 
         y[i] = cardano_root(x[i], h);
 }
 
-// Step 1, SSM_COEF_OU (v = rho x): Y = X / (1 - h rho) (Remark 4.3), taken as a
-// product with the reciprocal (FP64 division costs many FP64-pipe instructions,
-// and that pipe runs at 1/64 of the FP32 rate here), and the mean of Y that
-// step 2's b = lambda * mean needs -- summed in compensated FP32 per thread in the
-// FP32C form, in FP64 otherwise; blocks combine in FP64.
+// Step 1 of the sets whose measure enters through means (OU, GL1, GL2, POLY, CS),
+// all per particle against the frozen mu^X, whose moments mom (of X_n) are known:
+//   OU:   Y = X / (1 - h rho) (Remark 4.3), as a product with the reciprocal
+//         (an FP64 division costs many FP64-pipe instructions, and that pipe runs
+//         at 1/64 of the FP32 rate here);
+//   GL1:  Y + h Y^3 = X;  GL2: Y + h Y^3 = X + h c mean(X);
+//   POLY: Y = X / (1 - h gamma + h mean(X^2));  CS: V_Y + h V_Y^3 = V, X_Y = X;
+// and the mean of Y that step 2 needs -- summed in compensated FP32 per thread in
+// the FP32C form (whose cubic roots are cardano_gl32), in FP64 otherwise; blocks
+// combine in FP64.
 template <int D, bool F32>
 __global__ void __launch_bounds__(EUL_THREADS)
-k_ou_implicit(const double *__restrict__ x, double *__restrict__ y, int64_t N, int64_t Np, double rinv, double *mpart,
-              unsigned *ticket, double *ymean) {
+k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, int64_t N, int64_t Np, double h,
+              double p0, double p1, const double *__restrict__ xmom, double *mpart, unsigned *ticket,
+              double *ymean) {
     double m[D];
     float mh[D], ml[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) { m[c] = 0.0; mh[c] = 0.0f; ml[c] = 0.0f; }
+    double lin = 1.0, shift = 0.0;   // OU and POLY: the factor; GL2: the measure term
+    if (coef == SSM_COEF_OU) lin = 1.0 / (1.0 - h * p0);
+    if (coef == SSM_COEF_POLY) lin = 1.0 / (1.0 - h * p0 + h * xmom[D]);
+    if (coef == SSM_COEF_GL2) shift = h * p1 * xmom[0];
+    const bool cubic = coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_CS;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double v = x[c * Np + i] * rinv;
+            const double xv = x[c * Np + i];
+            double v;
+            if (cubic && c == 0) v = F32 ? cardano_gl32(xv + shift, h) : cardano_root_a(xv + shift, h, 1.0);
+            else if (coef == SSM_COEF_CS) v = xv;   // X part of (V, X): v = 0
+            else v = xv * lin;
             y[c * Np + i] = v;
             if (F32) two_sum_acc(mh[c], ml[c], f64_to_f32(v));
             else m[c] += v;
@@ -297,14 +332,13 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 template <int D, bool F32>
 __global__ void __launch_bounds__(EUL_THREADS, 4)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
-        double bscale, int coef, double lam, double eta, const double *__restrict__ ymean, int64_t N, int64_t Np,
-        double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep, double *mpart,
-        unsigned *ticket, double *mom, int *err, long long *counters) {
+        double bscale, int coef, double p0, double p1, double p2, const double *__restrict__ ymean, int64_t N,
+        int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
+        double *mpart, unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
-    const bool ou = coef == SSM_COEF_OU;
-    // b of particle i (OU: lambda mean(Y), the same for all particles)
-    auto drift = [&](int64_t i, int c) -> double {
-        if (ou) return lam * ymean[c];
+    const bool mm = is_moment_set(coef);
+    // b of particle i from the pair partial sums (pair sets)
+    auto pair_drift = [&](int64_t i, int c) -> double {
         double sm = 0.0;
         for (int k = 0; k < chunks; ++k) sm += part[((int64_t)k * D + c) * Np + i];
         return sm * bscale;
@@ -314,28 +348,34 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
     for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (F32) {
-        float hb_ou[D];
+        float ymf[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) hb_ou[c] = ou ? (float)(h * lam * ymean[c]) : 0.0f;
-        const float hf = (float)h, etaf = (float)eta, sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
+        for (int c = 0; c < D; ++c) ymf[c] = mm ? (float)ymean[c] : 0.0f;
+        const float hf = (float)h, p0f = (float)p0, p1f = (float)p1, p2f = (float)p2;
+        const float sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
         // X' = Y + inc for particle i; returns the FP32 powers 1..4 of X' (4 D values).
         // The loads are issued before the Philox and Box-Muller arithmetic they overlap.
         auto advance = [&](int64_t i, float (&p)[4 * D]) {
             double yv[D];
-            float hb[D];
+            float yf[D], hb[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 yv[c] = y[c * Np + i];
-                hb[c] = ou ? hb_ou[c] : hf * f64_to_f32(drift(i, c));
+                if (!mm) hb[c] = hf * f64_to_f32(pair_drift(i, c));
             }
+#pragma unroll
+            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32(yv[c]);
+            if (mm)
+#pragma unroll
+                for (int c = 0; c < D; ++c) hb[c] = hf * moment_b<float>(coef, c, yf, ymf, p0f, p1f);
             float dw[D];
             brownian32<D>(seed, i, n, sqh, fine_r, sqhf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const float yf = f64_to_f32(yv[c]);
-                const float inc = fmaf(sigma_of32(coef, yf, etaf), dw[c], hb[c]);
+                const float sg = mm ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : sigma_of32(coef, yf[c], p2f);
+                const float inc = fmaf(sg, dw[c], hb[c]);
                 x[c * Np + i] = yv[c] + f32_to_f64(inc);
-                const float v = yf + inc, v2 = v * v;
+                const float v = yf[c] + inc, v2 = v * v;
                 p[0 * D + c] = v;
                 p[1 * D + c] = v2;
                 p[2 * D + c] = v2 * v;
@@ -359,13 +399,20 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
 #pragma unroll
         for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] + (double)ml[k];
     } else {
+        double ym[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) ym[c] = mm ? ymean[c] : 0.0;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+            double yv[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) yv[c] = y[c * Np + i];
             double dw[D];
             brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const double yv = y[c * Np + i];
-                const double xn = yv + h * drift(i, c) + sigma_of(coef, yv, eta) * dw[c];
+                const double b = mm ? moment_b<double>(coef, c, yv, ym, p0, p1) : pair_drift(i, c);
+                const double sg = mm ? moment_sigma<double>(coef, c, yv, ym, p0, p1, p2) : sigma_of(coef, yv[c], p2);
+                const double xn = yv[c] + h * b + sg * dw[c];
                 x[c * Np + i] = xn;
                 add_powers<D>(m, c, xn);
             }
@@ -400,13 +447,16 @@ __global__ void k_soa_to_aos(const double *__restrict__ s, double *__restrict__ 
     }
 }
 // b of the last step, particle-major, from the drift partials.
-__global__ void k_stage_b(const double *__restrict__ part, int chunks, double bscale, int coef, double lam,
-                          const double *__restrict__ ymean, double *__restrict__ a, int d, int64_t N, int64_t Np) {
+__global__ void k_stage_b(const double *__restrict__ part, int chunks, double bscale, int coef, double p0, double p1,
+                          const double *__restrict__ ymean, const double *__restrict__ y, double *__restrict__ a,
+                          int d, int64_t N, int64_t Np) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N * d; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = k / d;
         const int c = (int)(k - i * d);
-        if (coef == SSM_COEF_OU) {
-            a[k] = lam * ymean[c];
+        if (is_moment_set(coef)) {
+            double yv[3] = {0.0, 0.0, 0.0}, ym[3] = {0.0, 0.0, 0.0};
+            for (int e = 0; e < d; ++e) { yv[e] = y[e * Np + i]; ym[e] = ymean[e]; }
+            a[k] = moment_b<double>(coef, c, yv, ym, p0, p1);
         } else {
             double s = 0.0;
             for (int q = 0; q < chunks; ++q) s += part[((int64_t)q * d + c) * Np + i];
@@ -488,18 +538,18 @@ cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_ou_implicit(ssm_ctx *c) {
-    const double rinv = 1.0 / (1.0 - c->h * c->opt.coef_params[0]);
+cudaError_t launch_mm_implicit(ssm_ctx *c) {
     const bool f32 = c->prec != SSM_FP64;
-#define SSM_OU(D) \
-    if (f32) k_ou_implicit<D, true><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, rinv, c->mpart, \
-                                                                          c->ticket, c->ymean); \
-    else k_ou_implicit<D, false><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->N, c->Np, rinv, c->mpart, \
-                                                                       c->ticket, c->ymean);
-    if (c->d == 1) { SSM_OU(1) }
-    else if (c->d == 2) { SSM_OU(2) }
-    else { SSM_OU(3) }
-#undef SSM_OU
+    const double p0 = c->opt.coef_params[0], p1 = c->opt.coef_params[1];
+#define SSM_MM(D) \
+    if (f32) k_mm_implicit<D, true><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
+                                                                          p1, c->mom, c->mpart, c->ticket, c->ymean); \
+    else k_mm_implicit<D, false><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
+                                                                       p1, c->mom, c->mpart, c->ticket, c->ymean);
+    if (c->d == 1) { SSM_MM(1) }
+    else if (c->d == 2) { SSM_MM(2) }
+    else { SSM_MM(3) }
+#undef SSM_MM
     return cudaGetLastError();
 }
 
@@ -533,10 +583,10 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const int fine_r = c->opt.fine_log2 > 0 ? (int)llround(c->h / (c->T / (double)(1ll << c->opt.fine_log2))) : 1;
     const double sqrt_hf = c->opt.fine_log2 > 0 ? sqrt(c->T / (double)(1ll << c->opt.fine_log2)) : 0.0;
     const int chunks = c->plan_drift.chunks;
-    const double lam = c->opt.coef_params[1], eta = c->opt.coef_params[2];
+    const double p0 = c->opt.coef_params[0], p1 = c->opt.coef_params[1], p2 = c->opt.coef_params[2];
     const bool f32 = c->prec != SSM_FP64;
 #define SSM_EUL(D, F) k_euler<D, F><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, c->coef, \
-        lam, eta, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, \
+        p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, \
         c->mom, c->err, c->counters)
     if (c->d == 1) { if (f32) SSM_EUL(1, true); else SSM_EUL(1, false); }
     else if (c->d == 2) { if (f32) SSM_EUL(2, true); else SSM_EUL(2, false); }
@@ -561,7 +611,8 @@ cudaError_t launch_soa_to_aos(const double *s, double *a, int d, int64_t N, int6
 }
 cudaError_t launch_stage_b(ssm_ctx *c, double bscale) {
     k_stage_b<<<gs_blocks(c->N * c->d, 256), 256, 0, c->st>>>(c->part, c->plan_drift.chunks, bscale, c->coef,
-                                                             c->opt.coef_params[1], c->ymean, c->stage, c->d, c->N, c->Np);
+                                                             c->opt.coef_params[0], c->opt.coef_params[1], c->ymean,
+                                                             c->y, c->stage, c->d, c->N, c->Np);
     return cudaGetLastError();
 }
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *out, cudaStream_t st) {

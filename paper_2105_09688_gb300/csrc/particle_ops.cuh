@@ -159,6 +159,41 @@ __device__ __forceinline__ void brownian32(uint64_t seed, int64_t i, long long n
     }
 }
 
+// Step-2 coefficients of the sets whose measure enters through means (OU and the
+// examples of §3.2-3.4), component c at Y = y[0..d-1], with m = mean(Y) per
+// component and p = the set's parameters:
+//   OU   (§3.4.1): b = lambda m,                 sigma = eta         (p = rho, lambda, eta)
+//   GL1  (§3.2 v1): b = s^2/2 y + c m,           sigma = s y          (p = s, c)
+//   GL2  (§3.2 v2): b = s^2/2 y,                 sigma = s y
+//   POLY (§3.3):    b = m,                        sigma = y           (p = gamma)
+//   CS   (§3.4, y = (V, X)): b = (1 + lambda (m_V - V), V), sigma = diag(s (m_V - V), 0)
+//                                                                     (p = lambda, s)
+// (CS with the sign of the paper's particle system, which flocks to the mean.)
+__host__ __device__ inline bool is_moment_set(int coef) {
+    return coef == SSM_COEF_OU || coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_POLY ||
+           coef == SSM_COEF_CS;
+}
+template <typename T>
+__device__ __forceinline__ T moment_b(int coef, int c, const T *y, const T *m, T p0, T p1) {
+    switch (coef) {
+    case SSM_COEF_GL1: return p0 * p0 / T(2) * y[0] + p1 * m[0];
+    case SSM_COEF_GL2: return p0 * p0 / T(2) * y[0];
+    case SSM_COEF_POLY: return m[0];
+    case SSM_COEF_CS: return c == 0 ? T(1) + p0 * (m[0] - y[0]) : y[0];
+    default: return p1 * m[c];   // OU
+    }
+}
+template <typename T>
+__device__ __forceinline__ T moment_sigma(int coef, int c, const T *y, const T *m, T p0, T p1, T p2) {
+    switch (coef) {
+    case SSM_COEF_GL1:
+    case SSM_COEF_GL2: return p0 * y[0];
+    case SSM_COEF_POLY: return y[0];
+    case SSM_COEF_CS: return c == 0 ? p1 * (m[0] - y[0]) : T(0);
+    default: return p2;   // OU
+    }
+}
+
 // Diffusion coefficient of each coefficient set, evaluated at Y (step 2).
 __device__ __forceinline__ double sigma_of(int coef, double y, double eta) {
     if (coef == SSM_COEF_CUBIC1D_GAUSS) return 0.4 * y + 0.1;
