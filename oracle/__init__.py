@@ -28,7 +28,7 @@ _c_int, _c_i64, _c_dbl, _c_u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double, 
 class Problem(ctypes.Structure):
     _fields_ = [("d", _c_int), ("coef", _c_int), ("N", _c_i64), ("h", _c_dbl), ("T", _c_dbl),
                 ("seed", _c_u64), ("p", _c_dbl * 4), ("x0_mean", _c_dbl), ("x0_std", _c_dbl),
-                ("fine_log2", _c_int)]
+                ("fine_log2", _c_int), ("measure_y", _c_int)]
 
 
 _LIB = None
@@ -59,6 +59,7 @@ def lib():
             "orc_moments": (None, [P, dp, dp]),
             "orc_run": (_c_int, [P, dp, _c_i64, _c_i64, dp, ctypes.POINTER(_c_i64)]),
             "orc_num_threads": (_c_int, []),
+            "orc_joint_residual_one": (None, [P, dp, dp, _c_i64, dp]),
             "orc_sample_step": (None, [P, dp, dp, ctypes.POINTER(_c_i64), _c_i64, _c_i64, dp]),
         }
         for name, (res, args) in sig.items():
@@ -74,8 +75,9 @@ def _dp(a):
 
 
 def problem(d, coef, N, h, T=1.0, seed=0, p=(0.0, 0.0, 0.0, 0.0), x0_mean=0.0, x0_std=1.0,
-            fine_log2=0):
+            fine_log2=0, measure_y=0):
     P = Problem()
+    P.measure_y = int(measure_y)
     P.d, P.coef, P.N, P.h, P.T, P.seed = int(d), int(coef), int(N), float(h), float(T), int(seed)
     for k in range(4):
         P.p[k] = float(p[k]) if k < len(p) else 0.0
@@ -172,6 +174,14 @@ def pair_sum_coupled(P, x, y_point):
     JS = np.empty(9)
     lib().orc_pair_sum_coupled(ctypes.byref(P), _dp(x), _dp(yp), _dp(S), _dp(JS))
     return S[:P.d].copy(), JS[:P.d * P.d].reshape(P.d, P.d)
+
+
+def joint_residual_one(P, x, y, i):
+    """G_i = Y_i - X_i - h v(Y_i, mu^Y) of step 1 against the measure of Y itself."""
+    x, y = _c(x, P), _c(y, P)
+    g = np.empty(3)
+    lib().orc_joint_residual_one(ctypes.byref(P), _dp(x), _dp(y), int(i), _dp(g))
+    return g[:P.d].copy()
 
 
 def implicit_step(P, x):

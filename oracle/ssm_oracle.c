@@ -58,6 +58,12 @@
  *   GL1, GL2, the V part of CS: y + h y^3 = x (+ h c mean(X) for GL2), one real
  *     root for every h > 0, by the same Cardano form and Newton correction.
  *   POLY: the equation is linear in y: y = x / (1 - h gamma + h mean(X^2)).
+ *   measure_y = 1 (coupled sets): step 1 with mu^Y in place of mu^X, the joint
+ *     system G(Y) = 0 in R^{dN}, G_i = Y_i - X_i - h v(Y_i, mu^Y) -- the earlier
+ *     implicit scheme that §1 contrasts with the SSM.  Newton's method on the whole
+ *     system with its exact dN x dN Jacobian (dense Gaussian elimination with
+ *     partial pivoting), step halving when the residual grows, start Y = X;
+ *     N d <= 1536.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), key = (seed mod 2^32, seed >> 32),
@@ -454,8 +460,139 @@ void orc_pair_sum_coupled(const orc_problem *P, const double *x, const double *y
     pair_sum_coupled(P, x, y, S, JS);
 }
 
+/* Joint residual G (dN) of step 1 against mu^Y and, optionally, its dense
+ * Jacobian J (dN x dN, row-major):
+ *   G_i = Y_i - X_i - h (-Y_i |Y_i|^2 + 0.5 S_i),  S_i = (1/N) sum_j (Y_j - Y_i) w_ij,
+ *   w_ij = 1 / (1 + |Y_j - Y_i|^2);
+ *   dS_i/dY_j = (1/N) (w I - 2 w^2 d d^T)  (j != i),  d = Y_j - Y_i,
+ *   dS_i/dY_i = -sum_{j != i} dS_i/dY_j  (the self term is identically zero). */
+static void joint_residual(const orc_problem *P, const double *x, const double *y, double *G, double *J)
+{
+    const int d = P->d;
+    const int64_t N = P->N, n = N * d;
+    if (J) memset(J, 0, sizeof(double) * (size_t)(n * n));
+    for (int64_t i = 0; i < N; ++i) {
+        const double *yi = y + d * i;
+        double S[3] = { 0, 0, 0 };
+        for (int64_t j = 0; j < N; ++j) {
+            double dd[3] = { 0, 0, 0 }, q = 1.0;
+            for (int a = 0; a < d; ++a) { dd[a] = y[d * j + a] - yi[a]; q += dd[a] * dd[a]; }
+            double w = 1.0 / q;
+            for (int a = 0; a < d; ++a) S[a] += dd[a] * w;
+            if (J && j != i)
+                for (int a = 0; a < d; ++a)
+                    for (int c = 0; c < d; ++c) {
+                        double g = ((a == c ? w : 0.0) - 2.0 * w * w * dd[a] * dd[c]) / (double)N;
+                        /* dG_i/dY_j = -h 0.5 dS_i/dY_j, and dS_i/dY_i gets -g */
+                        J[(d * i + a) * n + d * j + c] += -P->h * 0.5 * g;
+                        J[(d * i + a) * n + d * i + c] -= -P->h * 0.5 * g;
+                    }
+        }
+        double r2 = 0.0;
+        for (int a = 0; a < d; ++a) r2 += yi[a] * yi[a];
+        for (int a = 0; a < d; ++a) {
+            double v = -yi[a] * r2 + 0.5 * S[a] / (double)N;
+            G[d * i + a] = yi[a] - x[d * i + a] - P->h * v;
+        }
+        if (J)
+            for (int a = 0; a < d; ++a)
+                for (int c = 0; c < d; ++c) {
+                    double dv = -((a == c ? r2 : 0.0) + 2.0 * yi[a] * yi[c]);
+                    J[(d * i + a) * n + d * i + c] += (a == c ? 1.0 : 0.0) - P->h * dv;
+                }
+    }
+}
+
+/* Dense Gaussian elimination with partial pivoting: A s = r, A n x n (destroyed). */
+static int solve_dense(int64_t n, double *A, double *r, double *s)
+{
+    for (int64_t col = 0; col < n; ++col) {
+        int64_t piv = col;
+        for (int64_t row = col + 1; row < n; ++row)
+            if (fabs(A[row * n + col]) > fabs(A[piv * n + col])) piv = row;
+        if (A[piv * n + col] == 0.0) return -1;
+        if (piv != col) {
+            for (int64_t c = 0; c < n; ++c) { double t = A[col * n + c]; A[col * n + c] = A[piv * n + c]; A[piv * n + c] = t; }
+            double t = r[col]; r[col] = r[piv]; r[piv] = t;
+        }
+        for (int64_t row = col + 1; row < n; ++row) {
+            double f = A[row * n + col] / A[col * n + col];
+            if (f == 0.0) continue;
+            for (int64_t c = col; c < n; ++c) A[row * n + c] -= f * A[col * n + c];
+            r[row] -= f * r[col];
+        }
+    }
+    for (int64_t row = n - 1; row >= 0; --row) {
+        double acc = r[row];
+        for (int64_t c = row + 1; c < n; ++c) acc -= A[row * n + c] * s[c];
+        s[row] = acc / A[row * n + row];
+    }
+    return 0;
+}
+
+/* G_i of the joint system at the full state y (any N; for checks at large N). */
+void orc_joint_residual_one(const orc_problem *P, const double *x, const double *y, int64_t i, double *g)
+{
+    const int d = P->d;
+    const double *yi = y + (int64_t)d * i;
+    double S[3] = { 0, 0, 0 }, r2 = 0.0;
+    for (int64_t j = 0; j < P->N; ++j) {
+        double dd[3] = { 0, 0, 0 }, q = 1.0;
+        for (int a = 0; a < d; ++a) { dd[a] = y[(int64_t)d * j + a] - yi[a]; q += dd[a] * dd[a]; }
+        for (int a = 0; a < d; ++a) S[a] += dd[a] / q;
+    }
+    for (int a = 0; a < d; ++a) r2 += yi[a] * yi[a];
+    for (int a = 0; a < d; ++a)
+        g[a] = yi[a] - x[(int64_t)d * i + a] - P->h * (-yi[a] * r2 + 0.5 * S[a] / (double)P->N);
+}
+
+/* Step 1 against mu^Y: Newton on G(Y) = 0 from Y = X.  Returns the iterations, or
+ * -1 when it did not converge in 50 (or N d is beyond the dense limit). */
+static int joint_implicit_step(const orc_problem *P, const double *x, double *y)
+{
+    const int64_t n = P->N * (int64_t)P->d;
+    if (n > 1536) return -1;
+    double *G = (double *)malloc(sizeof(double) * (size_t)n), *Gt = (double *)malloc(sizeof(double) * (size_t)n);
+    double *J = (double *)malloc(sizeof(double) * (size_t)(n * n)), *s = (double *)malloc(sizeof(double) * (size_t)n);
+    double *yt = (double *)malloc(sizeof(double) * (size_t)n);
+    int result = -1;
+    memcpy(y, x, sizeof(double) * (size_t)n);
+    joint_residual(P, x, y, G, J);
+    for (int it = 1; it <= 50; ++it) {
+        double fn = 0.0, ymax = 0.0;
+        for (int64_t k = 0; k < n; ++k) fn = fabs(G[k]) > fn ? fabs(G[k]) : fn;
+        memcpy(Gt, G, sizeof(double) * (size_t)n);
+        if (solve_dense(n, J, Gt, s) != 0) break;
+        double lam = 1.0, gn = 0.0;
+        for (int half = 0; half < 40; ++half) {
+            for (int64_t k = 0; k < n; ++k) yt[k] = y[k] - lam * s[k];
+            joint_residual(P, x, yt, Gt, NULL);
+            gn = 0.0;
+            for (int64_t k = 0; k < n; ++k) gn = fabs(Gt[k]) > gn ? fabs(Gt[k]) : gn;
+            if (gn <= fn || half == 39) break;
+            lam *= 0.5;
+        }
+        double step = 0.0;
+        for (int64_t k = 0; k < n; ++k) {
+            step = fabs(lam * s[k]) > step ? fabs(lam * s[k]) : step;
+            y[k] = yt[k];
+            ymax = fabs(y[k]) > ymax ? fabs(y[k]) : ymax;
+        }
+        joint_residual(P, x, y, G, J);
+        if (step <= 1e-14 * (ymax > 1.0 ? ymax : 1.0)) { result = it; break; }
+    }
+    free(G); free(Gt); free(J); free(s); free(yt);
+    return result;
+}
+
 int orc_implicit_step(const orc_problem *P, const double *x, double *y, int *iters)
 {
+    if (P->measure_y && (P->coef == ORC_COEF_COUPLED3D || P->coef == ORC_COEF_COUPLED1D)) {
+        int it = joint_implicit_step(P, x, y);
+        if (iters)
+            for (int64_t i = 0; i < P->N; ++i) iters[i] = it;
+        return it < 0 ? (int)P->N : 0;
+    }
     const int64_t N = P->N;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)

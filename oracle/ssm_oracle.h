@@ -28,6 +28,8 @@ typedef struct {
     double x0_mean;   /* X_0 = x0_mean + x0_std * Z */
     double x0_std;
     int fine_log2;    /* 0: own grid; L > 0: Brownian path on the grid T 2^-L */
+    int measure_y;    /* coupled sets: 0 = step 1 against mu^X (the SSM); 1 = against
+                         mu^Y, the joint R^{dN} system of the earlier implicit scheme */
 } orc_problem;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -42,6 +44,7 @@ void orc_drift_one(const orc_problem *P, const double *y, int64_t i, double *b_o
 void orc_pair_sum_coupled(const orc_problem *P, const double *x, const double *y,
                           double *S, double *JS);
 int orc_implicit_step(const orc_problem *P, const double *x, double *y, int *iters);
+void orc_joint_residual_one(const orc_problem *P, const double *x, const double *y, int64_t i, double *g);
 void orc_explicit_step(const orc_problem *P, const double *y, int64_t n, double *xnext);
 void orc_sample_step(const orc_problem *P, const double *x, double *y, const int64_t *idx, int64_t n,
                      int64_t step, double *xout);
