@@ -501,6 +501,26 @@ def main():
         p.close()
 
     batched = bench_batched(torch, S, stream) if args.batched else None
+
+    # step 1 against mu^Y (the joint system of the earlier implicit scheme), same workload, FP32C
+    my = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+               precision=S.SSM_FP32C, measure_y=1)
+    for w in (0, 1):
+        pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
+        my.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"])
+    my.run_steps(1)
+    my.sync()
+    ms0 = my.stats()
+    mev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    mev[0].record(stream)
+    my.run_steps(3)
+    mev[1].record(stream)
+    mev[1].synchronize()
+    ms1 = my.stats()
+    mdt = mev[0].elapsed_time(mev[1]) / 1e3 / 3
+    measure_y = {"value": N_PART / mdt, "unit": "particle-steps/s", "ms_per_step": mdt * 1e3, "steps": 3,
+                 "passes_per_step": (ms1["newton_passes"] - ms0["newton_passes"]) / 3}
+    my.close()
     o_n = bench_o_n(torch, S, stream) if args.o_n else None
 
     kmax = 12
@@ -519,6 +539,7 @@ def main():
             "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
             "plain_fp64": fp64,
             "batched_form": batched,
+            "measure_y_form": measure_y,
             "o_n_kernels": o_n,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -95,8 +95,8 @@ typedef struct {
     int precision;          /* ssm_precision; default SSM_FP64 */
     double newton_tol;      /* step 1 stops when max_c |r_c| <= newton_tol, with
                                r = Y - X - h v(Y, mu^X); 0 = default: 1e-13 (FP64);
-                               FP32 forms: max(1e-10, 2^-27 h (1 + 8/sqrt(N))), i.e. 1e-10
-                               at h <= 2^-8, N >= 2^10, and the FP32 evaluation floor of
+                               FP32 forms: max(1e-10, 2^-27 h (1 + 64/sqrt(N))), i.e. 1e-10
+                               at h <= 2^-8, N >= 2^14, and the FP32 evaluation floor of
                                the residual at larger h or small N */
     int newton_kmax;        /* maximum N-body passes of one implicit step; default 12 */
     int fine_log2;          /* 0: dW on the step's own grid.  L > 0: the Brownian path
@@ -113,6 +113,12 @@ typedef struct {
     int tile_chunks;        /* 0 = tuned; else number of source chunks per pair pass */
     int ws_passes;          /* learned form: passes from the learned start before the
                                plain restart; default 4 */
+    int measure_y;          /* coupled sets: 0 (default) = step 1 against mu^X, the SSM of
+                               §2.3; 1 = step 1 against mu^Y, the joint R^{dN} system
+                               Y_i = X_i + h v(Y_i, mu^Y) of the earlier implicit scheme that
+                               §1 contrasts with the SSM, solved by block-Jacobi passes (each
+                               an O(N^2) pair pass at the common iterate) to newton_tol.
+                               Not with SSM_FP32C_LEARNED. */
 } ssm_opts;
 
 typedef struct {

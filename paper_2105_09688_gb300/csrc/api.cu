@@ -20,6 +20,8 @@ cudaError_t launch_mm_implicit(ssm_ctx *c);
 cudaError_t launch_newton_begin(ssm_ctx *c);
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32);
 cudaError_t launch_step_stats(ssm_ctx *c);
+cudaError_t launch_mi_begin(ssm_ctx *c);
+cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32);
 cudaError_t launch_euler(ssm_ctx *c, double bscale);
 cudaError_t launch_set_step(ssm_ctx *c, long long n);
 cudaError_t launch_aos_to_soa(const double *a, double *s, int d, int64_t N, int64_t Np, cudaStream_t st);
@@ -132,7 +134,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -173,6 +175,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.sconv = take(nt ? sizeof(double) * 3 * Np : 0);
     L.mom_prev = take(sizeof(double) * 12);
     L.rprev = take(nt ? sizeof(float) * Np : 0);
+    L.mif = take(nt ? sizeof(int) * (kmax + 2) : 0);
     L.total = o;
     return L;
 }
@@ -215,6 +218,8 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
         return SSM_EINVAL;
     }
     if (o.precision == SSM_FP32C_LEARNED && coef != SSM_COEF_COUPLED3D) return SSM_EINVAL;
+    if (o.measure_y != 0 && (o.measure_y != 1 || !is_coupled(coef) || o.precision == SSM_FP32C_LEARNED))
+        return SSM_EINVAL;
     // Theorem 2.3: h <= 1/(1 + 2 L_v) when L_v > -1/2; also 1 - h L_v > 0 for Lemma 4.1.
     if (Lv > -0.5 && h > 1.0 / (1.0 + 2.0 * Lv)) return SSM_EINVAL;
     const double M = T / h;
@@ -269,16 +274,27 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         return launch_euler(c, 0.0);
     }
     // SSM_COEF_COUPLED3D / SSM_COEF_COUPLED1D
+    if (c->opt.measure_y) {
+        // step 1 against mu^Y: every pass evaluates all particles at the common iterate
+        if ((e = launch_mi_begin(c)) != cudaSuccess) return e;
+        for (int k = 0; k < c->kmax; ++k) {
+            if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->y, c->y, c->act0, c->cnt + k, c->N, c->Np,
+                               1.0, c->part, c->st)) != cudaSuccess)
+                return e;
+            if ((e = launch_mi_pass(c, k, f32 ? 1 : 0)) != cudaSuccess) return e;
+        }
+    } else {
     if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
-    if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
-        if ((e = ws_forward_start(c)) != cudaSuccess) return e;
-    int *a_in = c->act0, *a_out = c->act1;
-    for (int k = 0; k < c->kmax; ++k) {
-        if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np, 1.0,
-                           c->part, c->st)) != cudaSuccess)
-            return e;
-        if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
-        int *t = a_in; a_in = a_out; a_out = t;
+        if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
+            if ((e = ws_forward_start(c)) != cudaSuccess) return e;
+        int *a_in = c->act0, *a_out = c->act1;
+        for (int k = 0; k < c->kmax; ++k) {
+            if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np,
+                               1.0, c->part, c->st)) != cudaSuccess)
+                return e;
+            if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
+            int *t = a_in; a_in = a_out; a_out = t;
+        }
     }
     if ((e = launch_step_stats(c)) != cudaSuccess) return e;
     if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale,
@@ -365,6 +381,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->sconv = (double *)(b + L.sconv);
     c->mom_prev = (double *)(b + L.mom_prev);
     c->rprev = (float *)(b + L.rprev);
+    c->mif = (int *)(b + L.mif);
     c->ws_loaded = 0;
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0

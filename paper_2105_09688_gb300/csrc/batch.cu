@@ -547,6 +547,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
     ssm_opts o;
     if (opts) o = *opts; else ssm_opts_default(&o);
     if (o.precision != SSM_FP64 && o.precision != SSM_FP32C) return SSM_EINVAL;
+    if (o.measure_y != 0) return SSM_EINVAL;   // the batched form steps the SSM (mu^X in step 1)
     if (o.newton_kmax <= 0) o.newton_kmax = 12;
     if (o.newton_kmax > 64) return SSM_EINVAL;
     for (int e = 0; e < n; ++e) {

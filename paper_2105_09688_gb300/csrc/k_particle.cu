@@ -305,6 +305,101 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
         atomicAdd((unsigned long long *)&counters[CNT_FALLBACKS], (unsigned long long)nrestart);
 }
 
+// ---------------------------------------------------------------------------
+// Step 1 against mu^Y (ssm_opts.measure_y): the joint system G(Y) = 0 in R^{dN},
+// G_i = Y_i - X_i - h v(Y_i, mu^Y), of the earlier implicit scheme that §1 sets the
+// SSM against.  Nonlinear block-Jacobi passes: pass k evaluates S_i and Sw_i at the
+// common iterate Y^k for every particle (the pair kernel with sources = targets =
+// Y^k), which is the exact joint residual G_i(Y^k).  When every particle is within
+// tol the step ends at Y^k; otherwise every particle moves to the root of its local
+// model with the others held at Y^k (the local solve of the SSM's step 1), into a
+// proposal array that k_mi_commit copies over Y.  The coupling through the other
+// particles is O(h/2) per pass, so a few passes reach tol from Y = X -- Krylov
+// acceleration of the outer iteration would not pay at these contraction rates.
+// flags[k] is set when some particle of pass k was not within tol.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_mi_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
+                           int *__restrict__ cnt, int *__restrict__ flags, int kmax, int64_t N, int64_t Np) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c * Np + i] = x[c * Np + i];
+        act[i] = (int)i;
+    }
+    if (i == 0) {
+        cnt[0] = (int)N;
+        for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
+        for (int k = 0; k <= kmax; ++k) flags[k] = 0;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *__restrict__ prop,
+            const int *__restrict__ cnt, const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h,
+            double tol, int fp32, int pass, int *__restrict__ flags, float *__restrict__ rprev, int *err) {
+    constexpr int NC = D + 1;
+    if (cnt[pass] == 0) return;   // converged at an earlier pass (grid-uniform)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool conv = true;
+    if (i < N) {
+        double S[D], Sw = 0.0, Y[D], X[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) S[c] = 0.0;
+        for (int k = 0; k < chunks; ++k) {
+            const double *pk = part + (int64_t)k * NC * Np + i;
+#pragma unroll
+            for (int c = 0; c < D; ++c) S[c] += pk[c * Np];
+            Sw += pk[D * Np];
+        }
+        const double invN = 1.0 / (double)N;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            S[c] *= invN;
+            Y[c] = y[c * Np + i];
+            X[c] = x[c * Np + i];
+        }
+        Sw *= invN;
+        if (fp32)   // numerators were taken at fl(Y_i): (y_j - Y_i) = (y_j - fl(Y_i)) - (Y_i - fl(Y_i))
+#pragma unroll
+            for (int c = 0; c < D; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
+        double yy = 0.0, rinf = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) yy += Y[c] * Y[c];
+        bool bad = !(yy < 1e300);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
+            if (!(r == r)) bad = true;
+            rinf = fmax(rinf, fabs(r));
+        }
+        if (bad) atomicOr(err, ERR_NONFINITE);
+        // FP32 sums: accepted at their evaluation floor as in the SSM's step 1
+        conv = bad || rinf <= tol || (fp32 && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)rprev[i]);
+        rprev[i] = (float)rinf;
+        double u[D];
+        local_root<D>(S, Sw, Y, X, h, u);
+#pragma unroll
+        for (int c = 0; c < D; ++c) prop[c * Np + i] = u[c];
+    }
+    if (__any_sync(0xffffffffu, !conv) && (threadIdx.x & 31) == 0) atomicOr(&flags[pass], 1);
+}
+
+template <int D>
+__global__ void k_mi_commit(double *__restrict__ y, const double *__restrict__ prop, int *__restrict__ cnt,
+                            const int *__restrict__ flags, int pass, int kmax, int64_t N, int64_t Np, int *err) {
+    if (cnt[pass] == 0 || flags[pass] == 0) return;   // done: Y^pass is the solution
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N)
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c * Np + i] = prop[c * Np + i];
+    if (i == 0) {
+        if (pass + 1 < kmax) cnt[pass + 1] = (int)N;
+        else atomicOr(err, ERR_NOCONV);
+    }
+}
+
 // Work counters of one implicit step (one thread).
 __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *counters) {
     long long rows = 0, npass = 0;
@@ -571,6 +666,25 @@ cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *a
     if (c->d == 1) SSM_UPD(1);
     else SSM_UPD(3);
 #undef SSM_UPD
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi_begin(ssm_ctx *c) {
+    if (c->d == 1)
+        k_mi_begin<1><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->mif, c->kmax, c->N, c->Np);
+    else
+        k_mi_begin<3><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->mif, c->kmax, c->N, c->Np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32) {
+#define SSM_MI(D) \
+    k_mi_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->stage, c->cnt, c->part, c->plan_newton.chunks, \
+                                                       c->N, c->Np, c->h, c->tol, fp32, pass, c->mif, c->rprev, c->err); \
+    k_mi_commit<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->y, c->stage, c->cnt, c->mif, pass, c->kmax, c->N, c->Np, c->err);
+    if (c->d == 1) { SSM_MI(1) }
+    else { SSM_MI(3) }
+#undef SSM_MI
     return cudaGetLastError();
 }
 

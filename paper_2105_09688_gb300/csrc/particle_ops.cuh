@@ -32,29 +32,11 @@ enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 
 // longer cuts it tenfold and the residual is within 64 tol, the iteration has
 // reached that floor and the particle is accepted (rprev holds the previous
 // pass's residual of this particle).
+// Root u of the local model u = X + h(-u|u|^2 + 0.5(S - Sw (u - Y))) by Newton with
+// the Sherman-Morrison inverse of a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw).
 template <int D>
-__device__ __forceinline__ int newton_update_particle(double *S, double Sw, double *Y, const double *X, double h,
-                                                      double tol, bool fp32_targets, int pass, int kmax,
-                                                      int restart_pass, float *rprev) {
-    if (fp32_targets)   // numerators were taken at fl(Y): (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y))
-#pragma unroll
-        for (int c = 0; c < D; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
-    double yy = 0.0;
-#pragma unroll
-    for (int c = 0; c < D; ++c) yy += Y[c] * Y[c];
-    double rinf = 0.0;
-    bool bad = !(yy < 1e300);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
-        if (!(r == r)) bad = true;
-        rinf = fmax(rinf, fabs(r));
-    }
-    if (bad) return UPD_NONFINITE;
-    if (rinf <= tol) return UPD_CONVERGED;
-    if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_CONVERGED;
-    *rprev = (float)rinf;
-    double u[D];
+__device__ __forceinline__ void local_root(const double *S, double Sw, const double *Y, const double *X, double h,
+                                           double *u) {
 #pragma unroll
     for (int c = 0; c < D; ++c) u[c] = Y[c];
     for (int it = 0; it < 30; ++it) {
@@ -79,6 +61,32 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
         }
         if (smax <= 1e-16 * umax) break;
     }
+}
+
+template <int D>
+__device__ __forceinline__ int newton_update_particle(double *S, double Sw, double *Y, const double *X, double h,
+                                                      double tol, bool fp32_targets, int pass, int kmax,
+                                                      int restart_pass, float *rprev) {
+    if (fp32_targets)   // numerators were taken at fl(Y): (x_j - Y) = (x_j - fl(Y)) - (Y - fl(Y))
+#pragma unroll
+        for (int c = 0; c < D; ++c) S[c] -= (Y[c] - (double)(float)Y[c]) * Sw;
+    double yy = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) yy += Y[c] * Y[c];
+    double rinf = 0.0;
+    bool bad = !(yy < 1e300);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double r = Y[c] - X[c] - h * (-Y[c] * yy + 0.5 * S[c]);
+        if (!(r == r)) bad = true;
+        rinf = fmax(rinf, fabs(r));
+    }
+    if (bad) return UPD_NONFINITE;
+    if (rinf <= tol) return UPD_CONVERGED;
+    if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_CONVERGED;
+    *rprev = (float)rinf;
+    double u[D];
+    local_root<D>(S, Sw, Y, X, h, u);
     // Residual bound at u without another pair pass.  G(u) = 0 is the local model;
     // r(u) - G(u) = -h/2 (S(u) - S(Y) + Sw (u - Y)), and by the mean value theorem
     // |S(u) - S(Y) + Sw (u - Y)| <= (||2 M2|| + |grad Sw| |u - Y|) |u - Y| with

@@ -98,3 +98,14 @@ def test_batch_rejects_bad_descriptors_before_touching_the_gpu(S, desc):
 def test_batch_rejects_unsupported_precision(S):
     with pytest.raises(S.SSMError):
         S.Batch([dict(d=1, N=10, h=0.25, T=1.0, seed=1)], precision=S.SSM_FP32C_LEARNED)
+
+
+def test_measure_y_option_is_validated(S):
+    """Step 1 against mu^Y exists for the coupled sets in the FP64 and FP32C forms."""
+    for coef, prec, flag in [(S.SSM_COEF_CUBIC1D_GAUSS, 0, 1), (S.SSM_COEF_OU, 0, 1),
+                             (S.SSM_COEF_COUPLED3D, 2, 1), (S.SSM_COEF_COUPLED3D, 0, 2)]:
+        d = 3 if coef == S.SSM_COEF_COUPLED3D else 1
+        o = S.ssm_opts_default(precision=prec, measure_y=flag)
+        with pytest.raises(S.SSMError) as e:
+            S.ssm_create(d, 10, 2.0 ** -6, 1.0, coef, 0, o)
+        assert e.value.status == S.SSM_EINVAL
