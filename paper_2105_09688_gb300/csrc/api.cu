@@ -175,7 +175,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.sconv = take(nt ? sizeof(double) * 3 * Np : 0);
     L.mom_prev = take(sizeof(double) * 12);
     L.rprev = take(nt ? sizeof(float) * Np : 0);
-    L.mif = take(nt ? sizeof(int) * (kmax + 2) : 0);
+    L.mif = take(nt ? sizeof(int) * 3 * (kmax + 2) : 0);
     L.total = o;
     return L;
 }

@@ -316,7 +316,13 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
 // proposal array that k_mi_commit copies over Y.  The coupling through the other
 // particles is O(h/2) per pass, so a few passes reach tol from Y = X -- Krylov
 // acceleration of the outer iteration would not pay at these contraction rates.
-// flags[k] is set when some particle of pass k was not within tol.
+// The pass that would only verify the last move is saved by a bound: with the
+// local bound b_i of the SSM's step 1 at the proposal (mean value theorem on the
+// particle's own pair terms) and every pair term f(d) = d / (1 + |d|^2) being
+// 1-Lipschitz, moving the other particles by D_j changes S_i by at most
+// (1/N) sum_j |D_j| <= max_j |D_j|, so |G_i(Y^{k+1})| <= b_i + (h/2) max_j |D_j|.
+// flags[k] is set when some particle of pass k was not within tol; flags[kmax+1+2k]
+// and flags[kmax+2+2k] hold max_i b_i and max_j |D_j| (non-negative floats as bits).
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_mi_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
@@ -330,7 +336,7 @@ __global__ void k_mi_begin(const double *__restrict__ x, double *__restrict__ y,
     if (i == 0) {
         cnt[0] = (int)N;
         for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
-        for (int k = 0; k <= kmax; ++k) flags[k] = 0;
+        for (int k = 0; k < 3 * (kmax + 1); ++k) flags[k] = 0;
     }
 }
 
@@ -338,11 +344,12 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *__restrict__ prop,
             const int *__restrict__ cnt, const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h,
-            double tol, int fp32, int pass, int *__restrict__ flags, float *__restrict__ rprev, int *err) {
+            double tol, int fp32, int pass, int kmax, int *__restrict__ flags, float *__restrict__ rprev, int *err) {
     constexpr int NC = D + 1;
     if (cnt[pass] == 0) return;   // converged at an earlier pass (grid-uniform)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool conv = true;
+    float lb = 0.0f, mv = 0.0f;
     if (i < N) {
         double S[D], Sw = 0.0, Y[D], X[D];
 #pragma unroll
@@ -380,23 +387,48 @@ k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *
         rprev[i] = (float)rinf;
         double u[D];
         local_root<D>(S, Sw, Y, X, h, u);
+        double uu = 0.0, du2 = 0.0, ginf = 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c) prop[c * Np + i] = u[c];
+        for (int c = 0; c < D; ++c) uu += u[c] * u[c];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            prop[c * Np + i] = u[c];
+            const double du = u[c] - Y[c];
+            ginf = fmax(ginf, fabs(u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * du));
+            du2 += du * du;
+        }
+        const double dn = sqrt(du2);
+        lb = (float)(0.5 * h * (0.5 + 0.65 * dn) * dn + ginf) * 1.0001f;   // rounded up past FP32
+        mv = (float)dn * 1.0001f;
     }
     if (__any_sync(0xffffffffu, !conv) && (threadIdx.x & 31) == 0) atomicOr(&flags[pass], 1);
+    for (int o = 16; o > 0; o >>= 1) {
+        lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+    }
+    if ((threadIdx.x & 31) == 0) {   // non-negative floats order like their bit patterns
+        atomicMax(&flags[kmax + 1 + 2 * pass], __float_as_int(lb));
+        atomicMax(&flags[kmax + 2 + 2 * pass], __float_as_int(mv));
+    }
 }
 
 template <int D>
 __global__ void k_mi_commit(double *__restrict__ y, const double *__restrict__ prop, int *__restrict__ cnt,
-                            const int *__restrict__ flags, int pass, int kmax, int64_t N, int64_t Np, int *err) {
+                            const int *__restrict__ flags, int pass, int kmax, int64_t N, int64_t Np, double h,
+                            double tol, int *err) {
     if (cnt[pass] == 0 || flags[pass] == 0) return;   // done: Y^pass is the solution
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N)
 #pragma unroll
         for (int c = 0; c < D; ++c) y[c * Np + i] = prop[c * Np + i];
     if (i == 0) {
-        if (pass + 1 < kmax) cnt[pass + 1] = (int)N;
-        else atomicOr(err, ERR_NOCONV);
+        const double lbmax = (double)__int_as_float(flags[kmax + 1 + 2 * pass]);
+        const double mvmax = (double)__int_as_float(flags[kmax + 2 + 2 * pass]);
+        const bool certified = lbmax + 0.5 * h * mvmax <= tol;   // done at the proposal
+        if (!certified) {
+            if (pass + 1 < kmax) cnt[pass + 1] = (int)N;
+            else atomicOr(err, ERR_NOCONV);
+        }
     }
 }
 
@@ -680,8 +712,10 @@ cudaError_t launch_mi_begin(ssm_ctx *c) {
 cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32) {
 #define SSM_MI(D) \
     k_mi_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->stage, c->cnt, c->part, c->plan_newton.chunks, \
-                                                       c->N, c->Np, c->h, c->tol, fp32, pass, c->mif, c->rprev, c->err); \
-    k_mi_commit<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->y, c->stage, c->cnt, c->mif, pass, c->kmax, c->N, c->Np, c->err);
+                                                       c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->mif, c->rprev, \
+                                                       c->err); \
+    k_mi_commit<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->y, c->stage, c->cnt, c->mif, pass, c->kmax, c->N, c->Np, \
+                                                       c->h, c->tol, c->err);
     if (c->d == 1) { SSM_MI(1) }
     else { SSM_MI(3) }
 #undef SSM_MI
