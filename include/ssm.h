@@ -73,9 +73,15 @@ typedef enum {
  *  SSM_COEF_CS (d = 2, x = (V, X); §3.4 Cucker-Smale), params (lambda, s):
  *      v = (-V^3, 0), b = (1 + lambda int (z - V) mu^V(dz), V),
  *      sigma = diag(s int (z - V) mu^V(dz), 0) -- the sign of the paper's particle
- *      system (a pull towards the mean velocity), not of its coefficient display. */
+ *      system (a pull towards the mean velocity), not of its coefficient display.
+ *  SSM_COEF_GLSTAB (d = 1; §3.4.2 Eq. (satblity:MV-GL-SDE)), params (gamma): the
+ *      stability example with gamma x moved from v to b (Remark on the L_v constraint):
+ *      v(x) = -(5/2 + gamma) x - x^3/4, b(y, mu) = int z mu(dz) + gamma y, sigma(y) = y.
+ *      Accepted for any h with 1 + h (5/2 + gamma) > 0 (a unique step-1 root): the
+ *      paper's study runs it outside Theorem 2.3's step bound on purpose. */
 typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU = 2, SSM_COEF_COUPLED1D = 3,
-               SSM_COEF_GL1 = 4, SSM_COEF_GL2 = 5, SSM_COEF_POLY = 6, SSM_COEF_CS = 7 } ssm_coef;
+               SSM_COEF_GL1 = 4, SSM_COEF_GL2 = 5, SSM_COEF_POLY = 6, SSM_COEF_CS = 7,
+               SSM_COEF_GLSTAB = 8 } ssm_coef;
 
 /* Arithmetic of a step.
  *  SSM_FP64: IEEE double throughout.
@@ -105,7 +111,8 @@ typedef struct {
                                at different h share one path (§3). */
     double x0_mean;         /* X_0 = x0_mean + x0_std Z, Z ~ N(0, I_d); default 0 */
     double x0_std;          /* default 1 */
-    double coef_params[4];  /* OU: rho, lambda, eta; GL1/GL2: s, c; POLY: gamma; CS: lambda, s */
+    double coef_params[4];  /* OU: rho, lambda, eta; GL1/GL2: s, c; POLY: gamma; CS: lambda, s;
+                               GLSTAB: gamma */
     void *stream;           /* cudaStream_t to enqueue on (borrowed); NULL = default stream */
     void *workspace;        /* optional caller-owned device memory, >= ssm_workspace_bytes(),
                                256-byte aligned; NULL = the context allocates */
@@ -211,6 +218,20 @@ ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int s
  * the host on the same source: out32[k] = (float)in[k], out64[k] = (double)out32[k]
  * for k < n (host arrays).  For checking them against another implementation. */
 ssm_status ssm_convert_check(const double *in, int64_t n, float *out32, double *out64);
+
+/* The constant beta of the mean-square stability theorem of §2 (label
+ * SSTM:stabilty, eq. (SSTM:beta formula)): for two SSM runs X, Z driven by the same
+ * noise, sup_i E|X_n^i - Z_n^i|^2 <= (1 + beta h)^n sup_i E|X_0^i - Z_0^i|^2, with
+ *   beta = ((2 L_v + A + 1 + L_vt) + h (L_vt A + B) + h^2 B L_vt) / (1 - h (2 L_v + 1)),
+ *   A = 2 sqrt(L_b) + 2 sqrt(L_bt) + L_s + L_st,  B = L_b + L_bt,
+ * from the one-sided Lipschitz constant L_v of v, the measure-Lipschitz constant
+ * L_vt of v and the squared Lipschitz constants (L_b, L_bt) and (L_s, L_st) of b and
+ * sigma in space and measure.  Host arithmetic, no device.  The bound needs
+ * 1 - h (2 L_v + 1) > 0 (the theorem's choice of h); beta is returned whenever the
+ * denominator is nonzero.  SSM_EINVAL for a negative constant (other than L_v), a
+ * non-finite input or a zero denominator. */
+ssm_status ssm_stability_beta(double Lv, double Lvt, double Lb, double Lbt, double Ls, double Lst, double h,
+                              double *beta);
 
 /* Step 1 for SSM_COEF_CUBIC1D_GAUSS alone: y[k] = the real root of
  * h y^3 + (1 - h) y - x[k] = 0 (Lemma 4.1's F_h for v = x - x^3), 0 < h < 1/3. */

@@ -21,6 +21,7 @@ COEF_GL1 = 4          # §3.2, SSM version 1: v = -x^3, b = s^2/2 y + c mean, si
 COEF_GL2 = 5          # §3.2, SSM version 2: v = -x^3 + c mean, b = s^2/2 y, sigma = s y
 COEF_POLY = 6         # §3.3: v = gamma x - x mean(x^2), b = mean, sigma = y
 COEF_CS = 7           # §3.4 Cucker-Smale, x = (V, X): v = (-V^3, 0), b = (1 + lambda (mean V - V), V)
+COEF_GLSTAB = 8       # §3.4.2: v = -(5/2 + gamma) x - x^3/4, b = mean + gamma y, sigma = y
 
 _c_int, _c_i64, _c_dbl, _c_u64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
 

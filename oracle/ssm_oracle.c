@@ -46,6 +46,9 @@
  *     The drift and diffusion integrals are taken with the sign of the paper's
  *     particle system, (lambda/N) sum_j (V_j - V_i): the flocking towards the mean
  *     that the section describes.
+ *   ORC_COEF_GLSTAB, d = 1, §3.4.2 Eq. (satblity:MV-GL-SDE), p = (gamma): the
+ *     stability example with a linear term gamma x moved from v to b,
+ *     v(x) = -(5/2 + gamma) x - x^3/4,  b(y, mu) = int z mu(dz) + gamma y,  sigma(y) = y.
  *
  * The implicit step is solved as follows.
  *   CUBIC1D_GAUSS: h y^3 + (1 - h) y - x = 0 has exactly one real root for
@@ -58,6 +61,8 @@
  *   GL1, GL2, the V part of CS: y + h y^3 = x (+ h c mean(X) for GL2), one real
  *     root for every h > 0, by the same Cardano form and Newton correction.
  *   POLY: the equation is linear in y: y = x / (1 - h gamma + h mean(X^2)).
+ *   GLSTAB: (h/4) y^3 + (1 + h (5/2 + gamma)) y = x, the same Cardano form (one real
+ *     root while 1 + h (5/2 + gamma) > 0).
  *   measure_y = 1 (coupled sets): step 1 with mu^Y in place of mu^X, the joint
  *     system G(Y) = 0 in R^{dN}, G_i = Y_i - X_i - h v(Y_i, mu^Y) -- the earlier
  *     implicit scheme that §1 contrasts with the SSM.  Newton's method on the whole
@@ -205,6 +210,10 @@ static void drift_b(const orc_problem *P, const double *y, const double *yi, dou
         b[0] = mean_power(P, y, 0, 1);
         return;
     }
+    if (P->coef == ORC_COEF_GLSTAB) {
+        b[0] = mean_power(P, y, 0, 1) + P->p[0] * yi[0];
+        return;
+    }
     if (P->coef == ORC_COEF_CS) {
         b[0] = 1.0 + P->p[0] * (mean_power(P, y, 0, 1) - yi[0]);
         b[1] = yi[0];
@@ -241,7 +250,7 @@ static void diffusion_times_dw(const orc_problem *P, const double *y, const doub
     const int d = P->d;
     if (P->coef == ORC_COEF_GL1 || P->coef == ORC_COEF_GL2) {
         out[0] = P->p[0] * yi[0] * dw[0];
-    } else if (P->coef == ORC_COEF_POLY) {
+    } else if (P->coef == ORC_COEF_POLY || P->coef == ORC_COEF_GLSTAB) {
         out[0] = yi[0] * dw[0];
     } else if (P->coef == ORC_COEF_CS) {
         out[0] = P->p[1] * (mean_power(P, y, 0, 1) - yi[0]) * dw[0];
@@ -399,6 +408,10 @@ int orc_implicit_point(const orc_problem *P, const double *x, const double *xi, 
     if (P->coef == ORC_COEF_CS) {
         y_out[0] = orc_cardano_gl(xi[0], P->h);
         y_out[1] = xi[1];
+        return 0;
+    }
+    if (P->coef == ORC_COEF_GLSTAB) {
+        y_out[0] = cardano_root(xi[0], P->h / 4.0, 1.0 + P->h * (2.5 + P->p[0]));
         return 0;
     }
     /* coupled sets: damped Newton from y = x_i. */

@@ -15,7 +15,7 @@
 #define ORC_PI 3.14159265358979323846
 
 enum { ORC_COEF_CUBIC1D_GAUSS = 0, ORC_COEF_COUPLED3D = 1, ORC_COEF_OU = 2, ORC_COEF_COUPLED1D = 3,
-       ORC_COEF_GL1 = 4, ORC_COEF_GL2 = 5, ORC_COEF_POLY = 6, ORC_COEF_CS = 7 };
+       ORC_COEF_GL1 = 4, ORC_COEF_GL2 = 5, ORC_COEF_POLY = 6, ORC_COEF_CS = 7, ORC_COEF_GLSTAB = 8 };
 
 typedef struct {
     int d;            /* space dimension: 1 or 3 (OU: any) */
@@ -24,7 +24,8 @@ typedef struct {
     double h;         /* step size */
     double T;         /* horizon (used for the fine Brownian grid) */
     uint64_t seed;    /* Philox key */
-    double p[4];      /* OU: rho, lambda, eta; GL1/GL2: sigma', c; POLY: gamma; CS: lambda, sigma' */
+    double p[4];      /* OU: rho, lambda, eta; GL1/GL2: sigma', c; POLY: gamma; CS: lambda, sigma';
+                         GLSTAB: gamma */
     double x0_mean;   /* X_0 = x0_mean + x0_std * Z */
     double x0_std;
     int fine_log2;    /* 0: own grid; L > 0: Brownian path on the grid T 2^-L */

@@ -23,14 +23,14 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_normals_fp32", "ssm_convert_check", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "load_ws",
+    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "SSM_COEF_GLSTAB", "ssm_stability_beta", "load_ws",
     "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
     "ssm_ws_num_params",
 ]
 
 SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
 SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU, SSM_COEF_COUPLED1D = 0, 1, 2, 3
-SSM_COEF_GL1, SSM_COEF_GL2, SSM_COEF_POLY, SSM_COEF_CS = 4, 5, 6, 7
+SSM_COEF_GL1, SSM_COEF_GL2, SSM_COEF_POLY, SSM_COEF_CS, SSM_COEF_GLSTAB = 4, 5, 6, 7, 8
 SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
 SSM_STAGE_Y, SSM_STAGE_B = 0, 1
 
@@ -89,6 +89,7 @@ _SIGS = {
     "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
     "ssm_normals_fp32": (_i32, [_u64, _i32, _i64, _i64, _i32, ctypes.POINTER(ctypes.c_float)]),
     "ssm_convert_check": (_i32, [_DP, _i64, ctypes.POINTER(ctypes.c_float), _DP]),
+    "ssm_stability_beta": (_i32, [_dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _dbl, _DP]),
     "ssm_cardano": (_i32, [_DP, _i64, _dbl, _DP]),
     "ssm_pair_pass": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "ssm_autotune": (_i32, [_vp, _DP]),
@@ -386,6 +387,14 @@ def ssm_normals(seed, d, N, step, stream):
     out = np.empty((int(N), int(d)))
     _check(lib().ssm_normals(int(seed), int(d), int(N), int(step), int(stream), _dp(out)), "ssm_normals")
     return out
+
+
+def ssm_stability_beta(Lv, Lvt, Lb, Lbt, Ls, Lst, h):
+    """beta of the mean-square stability theorem (see include/ssm.h)."""
+    out = _dbl()
+    _check(lib().ssm_stability_beta(float(Lv), float(Lvt), float(Lb), float(Lbt), float(Ls), float(Lst), float(h),
+                                    ctypes.byref(out)), "ssm_stability_beta")
+    return float(out.value)
 
 
 def ssm_convert_check(values):

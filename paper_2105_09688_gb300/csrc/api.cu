@@ -73,7 +73,7 @@ bool is_coupled(int coef) { return coef == SSM_COEF_COUPLED3D || coef == SSM_COE
 // Sets whose measure enters only through means: no pair sums, a per-particle step 1.
 bool is_moment(int coef) {
     return coef == SSM_COEF_OU || coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_POLY ||
-           coef == SSM_COEF_CS;
+           coef == SSM_COEF_CS || coef == SSM_COEF_GLSTAB;
 }
 int newton_kind(int d) { return d == 1 ? PK_NEWTON1 : PK_NEWTON3; }
 int drift_kind(int coef) { return (coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM_COEF_COUPLED1D) ? PK_DRIFT1 : PK_DRIFT3; }
@@ -214,6 +214,11 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
     } else if (coef == SSM_COEF_CS) {
         if (d != 2) return SSM_EINVAL;
         Lv = 0.0;                       // (-V^3, 0)
+    } else if (coef == SSM_COEF_GLSTAB) {
+        // the stability study runs outside Theorem 2.3's step bound on purpose (§3.4.2,
+        // h = 0.1 across gamma): only a unique step-1 root is required
+        if (d != 1 || !(1.0 + h * (2.5 + o.coef_params[0]) > 0.0)) return SSM_EINVAL;
+        Lv = -1.0;
     } else {
         return SSM_EINVAL;
     }
@@ -561,6 +566,20 @@ ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream
     if (e == cudaSuccess) e = cudaMemcpy(out, dz, sizeof(double) * d * N, cudaMemcpyDeviceToHost);
     cudaFree(dz);
     return cuda_status(e);
+}
+
+ssm_status ssm_stability_beta(double Lv, double Lvt, double Lb, double Lbt, double Ls, double Lst, double h,
+                              double *beta) {
+    if (!beta) return SSM_EINVAL;
+    const double in[7] = { Lv, Lvt, Lb, Lbt, Ls, Lst, h };
+    for (double v : in)
+        if (!isfinite(v)) return SSM_EINVAL;
+    if (Lvt < 0.0 || Lb < 0.0 || Lbt < 0.0 || Ls < 0.0 || Lst < 0.0 || !(h > 0.0)) return SSM_EINVAL;
+    const double A = 2.0 * sqrt(Lb) + 2.0 * sqrt(Lbt) + Ls + Lst, B = Lb + Lbt;
+    const double den = 1.0 - h * (2.0 * Lv + 1.0);
+    if (den == 0.0) return SSM_EINVAL;
+    *beta = ((2.0 * Lv + A + 1.0 + Lvt) + h * (Lvt * A + B) + h * h * B * Lvt) / den;
+    return SSM_OK;
 }
 
 ssm_status ssm_convert_check(const double *in, int64_t n, float *out32, double *out64) {

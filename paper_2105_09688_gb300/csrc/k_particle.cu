@@ -127,21 +127,21 @@ __device__ __forceinline__ double cardano_root_a(double x, double h, double a) {
 }
 __device__ __forceinline__ double cardano_root(double x, double h) { return cardano_root_a(x, h, 1.0 - h); }
 
-// The root of y + h y^3 = x for the FP32C forms: the same Cardano form in FP32
+// The root of h y^3 + a y = x for the FP32C forms: the same Cardano form in FP32
 // (relative error ~1e-6), then one Newton correction with the residual in FP64 and
 // the derivative in FP32, which leaves ~1e-13 relative (quadratic convergence, plus
 // the derivative's FP32 rounding times the first error), with five FP64 operations.
-__device__ __forceinline__ double cardano_gl32(double x, double h) {
-    const float xf = f64_to_f32(x), hf = (float)h;
-    const float p3 = 1.0f / (3.0f * hf), q = -xf / hf;
+__device__ __forceinline__ double cardano32_a(double x, double h, double a) {
+    const float xf = f64_to_f32(x), hf = (float)h, af = (float)a;
+    const float p3 = af / (3.0f * hf), q = -xf / hf;
     const float disc = 0.25f * q * q + p3 * p3 * p3;
     float u = cbrtf(0.5f * fabsf(q) + sqrtf(disc));
     if (q > 0.0f) u = -u;
     const float w = -p3 / u;
     const float y0 = -q / (u * u + p3 + w * w);
     const double yd = f32_to_f64(y0);
-    const double f = fma(h * yd, yd * yd, yd) - x;
-    const float fp = fmaf(3.0f * hf * y0, y0, 1.0f);
+    const double f = fma(h * yd, yd * yd, a * yd) - x;
+    const float fp = fmaf(3.0f * hf * y0, y0, af);
     return yd - f32_to_f64(f64_to_f32(f) / fp);
 }
 
@@ -157,8 +157,9 @@ __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, 
 //         at 1/64 of the FP32 rate here);
 //   GL1:  Y + h Y^3 = X;  GL2: Y + h Y^3 = X + h c mean(X);
 //   POLY: Y = X / (1 - h gamma + h mean(X^2));  CS: V_Y + h V_Y^3 = V, X_Y = X;
+//   GLSTAB: (h/4) Y^3 + (1 + h (5/2 + gamma)) Y = X;
 // and the mean of Y that step 2 needs -- summed in compensated FP32 per thread in
-// the FP32C form (whose cubic roots are cardano_gl32), in FP64 otherwise; blocks
+// the FP32C form (whose cubic roots are cardano32_a), in FP64 otherwise; blocks
 // combine in FP64.
 template <int D, bool F32>
 __global__ void __launch_bounds__(EUL_THREADS)
@@ -173,13 +174,16 @@ k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, in
     if (coef == SSM_COEF_OU) lin = 1.0 / (1.0 - h * p0);
     if (coef == SSM_COEF_POLY) lin = 1.0 / (1.0 - h * p0 + h * xmom[D]);
     if (coef == SSM_COEF_GL2) shift = h * p1 * xmom[0];
-    const bool cubic = coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_CS;
+    const bool cubic = coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_CS || coef == SSM_COEF_GLSTAB;
+    // the cubic h3 y^3 + a1 y = x + shift
+    const double h3 = coef == SSM_COEF_GLSTAB ? 0.25 * h : h;
+    const double a1 = coef == SSM_COEF_GLSTAB ? 1.0 + h * (2.5 + p0) : 1.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             const double xv = x[c * Np + i];
             double v;
-            if (cubic && c == 0) v = F32 ? cardano_gl32(xv + shift, h) : cardano_root_a(xv + shift, h, 1.0);
+            if (cubic && c == 0) v = F32 ? cardano32_a(xv + shift, h3, a1) : cardano_root_a(xv + shift, h3, a1);
             else if (coef == SSM_COEF_CS) v = xv;   // X part of (V, X): v = 0
             else v = xv * lin;
             y[c * Np + i] = v;

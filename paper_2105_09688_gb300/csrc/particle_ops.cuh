@@ -176,10 +176,11 @@ __device__ __forceinline__ void brownian32(uint64_t seed, int64_t i, long long n
 //   POLY (§3.3):    b = m,                        sigma = y           (p = gamma)
 //   CS   (§3.4, y = (V, X)): b = (1 + lambda (m_V - V), V), sigma = diag(s (m_V - V), 0)
 //                                                                     (p = lambda, s)
+//   GLSTAB (§3.4.2): b = m + gamma y,            sigma = y            (p = gamma)
 // (CS with the sign of the paper's particle system, which flocks to the mean.)
 __host__ __device__ inline bool is_moment_set(int coef) {
     return coef == SSM_COEF_OU || coef == SSM_COEF_GL1 || coef == SSM_COEF_GL2 || coef == SSM_COEF_POLY ||
-           coef == SSM_COEF_CS;
+           coef == SSM_COEF_CS || coef == SSM_COEF_GLSTAB;
 }
 template <typename T>
 __device__ __forceinline__ T moment_b(int coef, int c, const T *y, const T *m, T p0, T p1) {
@@ -188,6 +189,7 @@ __device__ __forceinline__ T moment_b(int coef, int c, const T *y, const T *m, T
     case SSM_COEF_GL2: return p0 * p0 / T(2) * y[0];
     case SSM_COEF_POLY: return m[0];
     case SSM_COEF_CS: return c == 0 ? T(1) + p0 * (m[0] - y[0]) : y[0];
+    case SSM_COEF_GLSTAB: return m[0] + p0 * y[0];
     default: return p1 * m[c];   // OU
     }
 }
@@ -196,7 +198,8 @@ __device__ __forceinline__ T moment_sigma(int coef, int c, const T *y, const T *
     switch (coef) {
     case SSM_COEF_GL1:
     case SSM_COEF_GL2: return p0 * y[0];
-    case SSM_COEF_POLY: return y[0];
+    case SSM_COEF_POLY:
+    case SSM_COEF_GLSTAB: return y[0];
     case SSM_COEF_CS: return c == 0 ? p1 * (m[0] - y[0]) : T(0);
     default: return p2;   // OU
     }
