@@ -58,7 +58,8 @@ def test_workspace_bytes_grows_with_N(S):
     (1, 100, 0.03, 1.0, 0),          # T/h not an integer
     (1, 100, -0.01, 1.0, 0),         # h <= 0
     (1, (1 << 26) + 1, 0.01, 1.0, 0),  # beyond the maximum N
-    (1, 100, 0.01, 1.0, 8),          # unknown coefficient set
+    (1, 100, 0.01, 1.0, 9),          # unknown coefficient set
+    (2, 100, 0.01, 1.0, 8),          # the GL stability set needs d = 1
     (1, 100, 0.01, 1.0, 7),          # Cucker-Smale needs d = 2
     (2, 100, 0.01, 1.0, 4),          # GL needs d = 1
 ])
