@@ -460,14 +460,18 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // added to the FP64 state with one FP64 add, and the moments from FP32 powers in
 // compensated FP32 per thread (FP64 across threads and blocks).  FP64 form: all FP64.
 // Compiled for RED_BLOCKS / 152 = 4 resident blocks per SM, so its fixed grid is one wave.
-template <int D, bool F32>
+// GEN: the moment sets other than OU (b and sigma depend on Y and its means through
+// moment_b / moment_sigma); otherwise the pair sets and OU, whose b is lambda mean(Y)
+// and sigma eta, the same for every particle.
+template <int D, bool F32, bool GEN>
 __global__ void __launch_bounds__(EUL_THREADS, 4)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
         double bscale, int coef, double p0, double p1, double p2, const double *__restrict__ ymean, int64_t N,
         int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
         double *mpart, unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
-    const bool mm = is_moment_set(coef);
+    const bool ou = coef == SSM_COEF_OU;
+    const bool mm = GEN || ou;
     // b of particle i from the pair partial sums (pair sets)
     auto pair_drift = [&](int64_t i, int c) -> double {
         double sm = 0.0;
@@ -479,9 +483,12 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
     for (int k = 0; k < 4 * D; ++k) m[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (F32) {
-        float ymf[D];
+        float ymf[D], hb_ou[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) ymf[c] = mm ? (float)ymean[c] : 0.0f;
+        for (int c = 0; c < D; ++c) {
+            ymf[c] = mm ? (float)ymean[c] : 0.0f;
+            hb_ou[c] = ou ? (float)(h * p1 * ymean[c]) : 0.0f;
+        }
         const float hf = (float)h, p0f = (float)p0, p1f = (float)p1, p2f = (float)p2;
         const float sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
         // X' = Y + inc for particle i; returns the FP32 powers 1..4 of X' (4 D values).
@@ -492,18 +499,18 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 yv[c] = y[c * Np + i];
-                if (!mm) hb[c] = hf * f64_to_f32(pair_drift(i, c));
+                if (!GEN) hb[c] = ou ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) yf[c] = f64_to_f32(yv[c]);
-            if (mm)
+            if (GEN)
 #pragma unroll
                 for (int c = 0; c < D; ++c) hb[c] = hf * moment_b<float>(coef, c, yf, ymf, p0f, p1f);
             float dw[D];
             brownian32<D>(seed, i, n, sqh, fine_r, sqhf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const float sg = mm ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : sigma_of32(coef, yf[c], p2f);
+                const float sg = GEN ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : sigma_of32(coef, yf[c], p2f);
                 const float inc = fmaf(sg, dw[c], hb[c]);
                 x[c * Np + i] = yv[c] + f32_to_f64(inc);
                 const float v = yf[c] + inc, v2 = v * v;
@@ -541,8 +548,8 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
             brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const double b = mm ? moment_b<double>(coef, c, yv, ym, p0, p1) : pair_drift(i, c);
-                const double sg = mm ? moment_sigma<double>(coef, c, yv, ym, p0, p1, p2) : sigma_of(coef, yv[c], p2);
+                const double b = GEN ? moment_b<double>(coef, c, yv, ym, p0, p1) : ou ? p1 * ym[c] : pair_drift(i, c);
+                const double sg = GEN ? moment_sigma<double>(coef, c, yv, ym, p0, p1, p2) : sigma_of(coef, yv[c], p2);
                 const double xn = yv[c] + h * b + sg * dw[c];
                 x[c * Np + i] = xn;
                 add_powers<D>(m, c, xn);
@@ -737,12 +744,15 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const int chunks = c->plan_drift.chunks;
     const double p0 = c->opt.coef_params[0], p1 = c->opt.coef_params[1], p2 = c->opt.coef_params[2];
     const bool f32 = c->prec != SSM_FP64;
-#define SSM_EUL(D, F) k_euler<D, F><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, c->coef, \
-        p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, c->ticket, \
-        c->mom, c->err, c->counters)
-    if (c->d == 1) { if (f32) SSM_EUL(1, true); else SSM_EUL(1, false); }
-    else if (c->d == 2) { if (f32) SSM_EUL(2, true); else SSM_EUL(2, false); }
-    else { if (f32) SSM_EUL(3, true); else SSM_EUL(3, false); }
+    const bool gen = is_moment_set(c->coef) && c->coef != SSM_COEF_OU;   // d = 1 or 2 only
+#define SSM_EUL(D, F, G) k_euler<D, F, G><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
+        c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, \
+        c->ticket, c->mom, c->err, c->counters)
+#define SSM_EUL_G(D, G) { if (f32) SSM_EUL(D, true, G); else SSM_EUL(D, false, G); }
+    if (c->d == 1) { if (gen) SSM_EUL_G(1, true) else SSM_EUL_G(1, false) }
+    else if (c->d == 2) { if (gen) SSM_EUL_G(2, true) else SSM_EUL_G(2, false) }
+    else SSM_EUL_G(3, false)
+#undef SSM_EUL_G
 #undef SSM_EUL
     k_advance<<<1, 1, 0, c->st>>>(c->dstep, c->counters, c->N);
     return cudaGetLastError();
