@@ -42,10 +42,10 @@ FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expan
 # N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), valid only for the
 # kernel sources it was measured on (their SHA-256 below); otherwise the roofline's
 # traffic is null.
-MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 8, 1 << 18), "bytes": 13293312 + 2779392,
+MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 8, 1 << 18), "bytes": 12706560 + 2779136,
                     "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu",
                                 "paper_2105_09688_gb300/csrc/ssm_device.cuh"),
-                    "sha256": "83792ea6f36f37c0218fea8679ca465e9b4c34e71c4bd2a20765e3df87f9d236"}
+                    "sha256": "c79e1277407735e4f2d3063126444bd2587d67dcdba36f5ba413cb93889d2961"}
 
 
 def measured_traffic(kernel, kind, threads, rpt, n):
@@ -220,21 +220,9 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def batch_descs(S):
-    """The 64-ensemble batched workload: N_e = round(2^(10 + 6 u_e)) with u_e the FP64
-    uniform of Philox(seed 3, counter (e, 0, 2, 0)), d_e = 1 for e < 32 else 3,
-    h_e = 2^-(4 + e mod 7), T = 1, seed 1000 + e."""
-    out = []
-    for e in range(64):
-        w = S.ssm_philox(3, [[e, 0, 2, 0]])[0]
-        u = (((int(w[0]) << 32 | int(w[1])) >> 11) + 1) * 2.0 ** -53
-        out.append(dict(d=1 if e < 32 else 3, N=int(round(2.0 ** (10 + 6 * u))), h=2.0 ** -(4 + e % 7), T=1.0,
-                        seed=1000 + e))
-    return out
-
-
 def bench_batched(torch, S, stream):
-    descs = batch_descs(S)
+    from paper_2105_09688_gb300.convergence import mixed_ensembles
+    descs = mixed_ensembles()      # 64 ensembles, N_e log-uniform in [2^10, 2^16], d = 1 and 3
     b = S.Batch(descs, stream=stream, precision=S.SSM_FP32C)
     best = b.autotune()
     units = sum(d["N"] * round(d["T"] / d["h"]) for d in descs)
@@ -280,7 +268,7 @@ def bench_o_n(torch, S, stream, steps=5, warmup=3):
     Y read and X written by step 2 (FP64 SoA)."""
     peak, basis = hbm_peak_gbs()
     N = 1 << ON_LOG2N
-    out = {"workload": "OU d=3 N=2^26 h=2^-6 (k_ou_implicit + k_euler per step)",
+    out = {"workload": "OU d=3 N=2^26 h=2^-6 (k_mm_implicit + k_euler per step)",
            "bytes_per_particle_step": ON_BYTES_PER_PARTICLE_STEP, "peak_gbs": peak, "peak_basis": basis}
     for name, prec in (("fp64", S.SSM_FP64), ("fp32c", S.SSM_FP32C)):
         try:
