@@ -91,7 +91,7 @@ typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU =
  *      double.  Step 2 draws the same Philox words but evaluates the Box-Muller
  *      transform in FP32 (|z error| < 5e-6) and forms the increment h b + sigma dW
  *      in FP32 before adding it to the FP64 state; the moments are FP32 powers
- *      summed in compensated FP32 per thread and in double across threads.
+ *      summed in compensated (Kahan) FP32 per thread and in double across threads.
  *      X_0 is drawn in FP64 in both forms.
  *  SSM_FP32C_LEARNED: SSM_FP32C with a learned initial guess for step 1
  *      (SSM_COEF_COUPLED3D only; load weights with ssm_ws_load). */
@@ -210,13 +210,17 @@ ssm_status ssm_philox(uint64_t seed, const uint32_t *ctr, int64_t n, uint32_t *o
 ssm_status ssm_normals(uint64_t seed, int d, int64_t N, int64_t step, int stream, double *out);
 
 /* The same normals as the FP32C forms evaluate them (FP32 Box-Muller of the same
- * Philox uniforms; |error| < 5e-6 against ssm_normals), out[N*d] on the host. */
+ * Philox uniforms, with the library's own FP32 log and cos/sin of pi a; |error| <
+ * 5e-6 against ssm_normals), out[N*d] on the host. */
 ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int stream, float *out);
 
 /* The binary64 -> binary32 (round to nearest even) and binary32 -> binary64
  * conversions that the FP32C kernels perform with integer instructions, run on
  * the host on the same source: out32[k] = (float)in[k], out64[k] = (double)out32[k]
- * for k < n (host arrays).  For checking them against another implementation. */
+ * for k < n (host arrays), except that inputs of magnitude below 2^-126 (the
+ * binary32 subnormal range and below) give a zero of the same sign.  Overflow
+ * gives infinity, NaN stays NaN.  For checking them against another
+ * implementation. */
 ssm_status ssm_convert_check(const double *in, int64_t n, float *out32, double *out64);
 
 /* The constant beta of the mean-square stability theorem of §2 (label

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include "particle_ops.cuh"
 #include "ssm_device.cuh"
 
@@ -131,6 +132,7 @@ __device__ __forceinline__ double cardano_root(double x, double h) { return card
 // (relative error ~1e-6), then one Newton correction with the residual in FP64 and
 // the derivative in FP32, which leaves ~1e-13 relative (quadratic convergence, plus
 // the derivative's FP32 rounding times the first error), with five FP64 operations.
+template <bool A1>   // A1: a = 1 (a y then needs no FP64 multiply)
 __device__ __forceinline__ double cardano32_a(double x, double h, double a) {
     const float xf = f64_to_f32(x), hf = (float)h, af = (float)a;
     const float p3 = af / (3.0f * hf), q = -xf / hf;
@@ -140,7 +142,7 @@ __device__ __forceinline__ double cardano32_a(double x, double h, double a) {
     const float w = -p3 / u;
     const float y0 = -q / (u * u + p3 + w * w);
     const double yd = f32_to_f64(y0);
-    const double f = fma(h * yd, yd * yd, a * yd) - x;
+    const double f = fma(h * yd, yd * yd, A1 ? yd : a * yd) - x;
     const float fp = fmaf(3.0f * hf * y0, y0, af);
     return yd - f32_to_f64(f64_to_f32(f) / fp);
 }
@@ -178,18 +180,51 @@ k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, in
     // the cubic h3 y^3 + a1 y = x + shift
     const double h3 = coef == SSM_COEF_GLSTAB ? 0.25 * h : h;
     const double a1 = coef == SSM_COEF_GLSTAB ? 1.0 + h * (2.5 + p0) : 1.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    auto add = [&](int c, double v) {
+        if (F32) two_sum_acc(mh[c], ml[c], f64_to_f32(v));
+        else m[c] += v;
+    };
+    // The loop is compiled once per (LIN: the linear sets, SHIFT: GL2's measure term,
+    // A1: a1 = 1), so no FP64 operation that a set does not need is issued, not even
+    // predicated off (the FP64 pipe bounds this kernel in the FP32C form).  Two
+    // particles per iteration, both loaded before either is used (memory-level
+    // parallelism for this streaming kernel).
+    auto sweep = [&](auto lin_t, auto shift_t, auto a1_t) {
+        constexpr bool LIN = decltype(lin_t)::value, SHIFT = decltype(shift_t)::value, A1 = decltype(a1_t)::value;
+        auto root = [&](int c, double xv) -> double {
+            if (LIN) return xv * lin;
+            if (c > 0) return xv;   // X part of Cucker-Smale's (V, X): v = 0
+            const double xs = SHIFT ? xv + shift : xv;
+            return F32 ? cardano32_a<A1>(xs, h3, a1) : cardano_root_a(xs, h3, a1);
+        };
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += 2 * stride) {
+            const bool two = i + stride < N;
+            double xa[D], xb[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const double xv = x[c * Np + i];
-            double v;
-            if (cubic && c == 0) v = F32 ? cardano32_a(xv + shift, h3, a1) : cardano_root_a(xv + shift, h3, a1);
-            else if (coef == SSM_COEF_CS) v = xv;   // X part of (V, X): v = 0
-            else v = xv * lin;
-            y[c * Np + i] = v;
-            if (F32) two_sum_acc(mh[c], ml[c], f64_to_f32(v));
-            else m[c] += v;
+            for (int c = 0; c < D; ++c) {
+                xa[c] = x[c * Np + i];
+                xb[c] = two ? x[c * Np + i + stride] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const double va = root(c, xa[c]);
+                y[c * Np + i] = va;
+                add(c, va);
+                if (two) {
+                    const double vb = root(c, xb[c]);
+                    y[c * Np + i + stride] = vb;
+                    add(c, vb);
+                }
+            }
         }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (!cubic) sweep(T_{}, F_{}, T_{});                      // OU, POLY
+    else if (coef == SSM_COEF_GL2) sweep(F_{}, T_{}, T_{});
+    else if (coef == SSM_COEF_GLSTAB) sweep(F_{}, F_{}, F_{});
+    else sweep(F_{}, F_{}, T_{});                             // GL1, CS
     if (F32)
 #pragma unroll
         for (int c = 0; c < D; ++c) m[c] = (double)mh[c] + (double)ml[c];
@@ -458,20 +493,22 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // ---------------------------------------------------------------------------
 // FP32C form (F32): dW from the FP32 transform, the increment h b + sigma dW in FP32
 // added to the FP64 state with one FP64 add, and the moments from FP32 powers in
-// compensated FP32 per thread (FP64 across threads and blocks).  FP64 form: all FP64.
-// Compiled for RED_BLOCKS / 152 = 4 resident blocks per SM, so its fixed grid is one wave.
-// GEN: the moment sets other than OU (b and sigma depend on Y and its means through
-// moment_b / moment_sigma); otherwise the pair sets and OU, whose b is lambda mean(Y)
-// and sigma eta, the same for every particle.
-template <int D, bool F32, bool GEN>
-__global__ void __launch_bounds__(EUL_THREADS, 4)
+// Kahan-compensated FP32 per thread (FP64 across threads and blocks).  FP64 form:
+// all FP64.  Compiled for EUL_MIN_BLOCKS resident blocks per SM and launched on
+// EUL_BLOCKS blocks, one wave.
+// FAM, the coefficient family, fixed at compile time so that each instance carries
+// only its own branch: EUL_PAIR (b from the pair partial sums, sigma per particle),
+// EUL_OU (b = lambda mean(Y), sigma = eta, the same for every particle), EUL_GEN
+// (the other moment sets: b and sigma from Y and its means, moment_b / moment_sigma).
+enum : int { EUL_PAIR = 0, EUL_OU = 1, EUL_GEN = 2 };
+template <int D, bool F32, int FAM>
+__global__ void __launch_bounds__(EUL_THREADS, EUL_MIN_BLOCKS)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
         double bscale, int coef, double p0, double p1, double p2, const double *__restrict__ ymean, int64_t N,
         int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
         double *mpart, unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
-    const bool ou = coef == SSM_COEF_OU;
-    const bool mm = GEN || ou;
+    constexpr bool GEN = FAM == EUL_GEN, OU = FAM == EUL_OU, MM = FAM != EUL_PAIR;
     // b of particle i from the pair partial sums (pair sets)
     auto pair_drift = [&](int64_t i, int c) -> double {
         double sm = 0.0;
@@ -486,8 +523,8 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
         float ymf[D], hb_ou[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            ymf[c] = mm ? (float)ymean[c] : 0.0f;
-            hb_ou[c] = ou ? (float)(h * p1 * ymean[c]) : 0.0f;
+            ymf[c] = MM ? (float)ymean[c] : 0.0f;
+            hb_ou[c] = OU ? (float)(h * p1 * ymean[c]) : 0.0f;
         }
         const float hf = (float)h, p0f = (float)p0, p1f = (float)p1, p2f = (float)p2;
         const float sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
@@ -499,7 +536,7 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 yv[c] = y[c * Np + i];
-                if (!GEN) hb[c] = ou ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
+                if (!GEN) hb[c] = OU ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) yf[c] = f64_to_f32(yv[c]);
@@ -510,7 +547,7 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
             brownian32<D>(seed, i, n, sqh, fine_r, sqhf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const float sg = GEN ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : sigma_of32(coef, yf[c], p2f);
+                const float sg = GEN ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : OU ? p2f : sigma_of32(coef, yf[c], p2f);
                 const float inc = fmaf(sg, dw[c], hb[c]);
                 x[c * Np + i] = yv[c] + f32_to_f64(inc);
                 const float v = yf[c] + inc, v2 = v * v;
@@ -523,23 +560,19 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
         float mh[4 * D], ml[4 * D];
 #pragma unroll
         for (int k = 0; k < 4 * D; ++k) { mh[k] = 0.0f; ml[k] = 0.0f; }
-        // two particles per iteration: their powers are added before the compensated sum
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += 2 * stride) {
-            float p[4 * D], q[4 * D];
+#pragma unroll 1
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+            float p[4 * D];
             advance(i, p);
-            if (i + stride < N) advance(i + stride, q);
-            else
 #pragma unroll
-                for (int k = 0; k < 4 * D; ++k) q[k] = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4 * D; ++k) two_sum_acc(mh[k], ml[k], p[k] + q[k]);
+            for (int k = 0; k < 4 * D; ++k) kahan_acc(mh[k], ml[k], p[k]);
         }
 #pragma unroll
-        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] + (double)ml[k];
+        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] - (double)ml[k];
     } else {
         double ym[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) ym[c] = mm ? ymean[c] : 0.0;
+        for (int c = 0; c < D; ++c) ym[c] = MM ? ymean[c] : 0.0;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
             double yv[D];
 #pragma unroll
@@ -548,7 +581,7 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
             brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const double b = GEN ? moment_b<double>(coef, c, yv, ym, p0, p1) : ou ? p1 * ym[c] : pair_drift(i, c);
+                const double b = GEN ? moment_b<double>(coef, c, yv, ym, p0, p1) : OU ? p1 * ym[c] : pair_drift(i, c);
                 const double sg = GEN ? moment_sigma<double>(coef, c, yv, ym, p0, p1, p2) : sigma_of(coef, yv[c], p2);
                 const double xn = yv[c] + h * b + sg * dw[c];
                 x[c * Np + i] = xn;
@@ -744,14 +777,15 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const int chunks = c->plan_drift.chunks;
     const double p0 = c->opt.coef_params[0], p1 = c->opt.coef_params[1], p2 = c->opt.coef_params[2];
     const bool f32 = c->prec != SSM_FP64;
-    const bool gen = is_moment_set(c->coef) && c->coef != SSM_COEF_OU;   // d = 1 or 2 only
-#define SSM_EUL(D, F, G) k_euler<D, F, G><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
+    // families by dimension: d = 1 pair sets, OU, GL/POLY/GLSTAB; d = 2 OU, CS; d = 3 pair sets, OU
+    const int fam = c->coef == SSM_COEF_OU ? EUL_OU : is_moment_set(c->coef) ? EUL_GEN : EUL_PAIR;
+#define SSM_EUL(D, F, G) k_euler<D, F, G><<<EUL_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
         c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, \
         c->ticket, c->mom, c->err, c->counters)
 #define SSM_EUL_G(D, G) { if (f32) SSM_EUL(D, true, G); else SSM_EUL(D, false, G); }
-    if (c->d == 1) { if (gen) SSM_EUL_G(1, true) else SSM_EUL_G(1, false) }
-    else if (c->d == 2) { if (gen) SSM_EUL_G(2, true) else SSM_EUL_G(2, false) }
-    else SSM_EUL_G(3, false)
+    if (c->d == 1) { if (fam == EUL_GEN) SSM_EUL_G(1, EUL_GEN) else if (fam == EUL_OU) SSM_EUL_G(1, EUL_OU) else SSM_EUL_G(1, EUL_PAIR) }
+    else if (c->d == 2) { if (fam == EUL_GEN) SSM_EUL_G(2, EUL_GEN) else SSM_EUL_G(2, EUL_OU) }
+    else { if (fam == EUL_OU) SSM_EUL_G(3, EUL_OU) else SSM_EUL_G(3, EUL_PAIR) }
 #undef SSM_EUL_G
 #undef SSM_EUL
     k_advance<<<1, 1, 0, c->st>>>(c->dstep, c->counters, c->N);

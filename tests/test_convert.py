@@ -1,6 +1,7 @@
 """The binary64 <-> binary32 conversions the FP32C kernels do with integer
 instructions (IEEE 754 bit manipulation, round to nearest even), run on the host
-through the library and compared bit for bit with numpy's conversions."""
+through the library and compared bit for bit with numpy's conversions.  Inputs
+below the binary32 normal range (|v| < 2^-126) give a zero of the input's sign."""
 import numpy as np
 import pytest
 
@@ -34,8 +35,18 @@ def test_double_to_float_matches_numpy_bit_for_bit(S):
     o32, _ = S.ssm_convert_check(v)
     with np.errstate(over="ignore"):
         ref = v.astype(np.float32)
+    tiny = np.abs(v) < np.finfo(np.float32).tiny
+    ref[tiny] = np.copysign(np.float32(0.0), v[tiny]).astype(np.float32)
+    assert tiny.sum() > 1000 and (~tiny).sum() > 100000
     same = (o32.view(np.uint32) == ref.view(np.uint32)) | (np.isnan(o32) & np.isnan(ref))
     assert same.all(), v[~same][:5]
+
+
+def test_below_the_normal_range_gives_a_signed_zero(S):
+    v = np.array([2.0 ** -126 * (1 - 2 ** -30), -2.0 ** -127, 2.0 ** -149, -2.0 ** -1074, 0.0, -0.0, 1e-300])
+    o32, o64 = S.ssm_convert_check(v)
+    assert (o32 == 0).all() and (np.signbit(o32) == np.signbit(v)).all()
+    assert (o64 == 0).all() and (np.signbit(o64) == np.signbit(v)).all()
 
 
 def test_float_to_double_is_exact(S):

@@ -114,9 +114,12 @@ def test_learned_start_keeps_the_roots_and_saves_passes(S, trained):
     N, seed, K = 4096, 7, 24
     xp, sp = _run(S, N, seed, K, S.SSM_FP32C)
     xl, sl = _run(S, N, seed, K, S.SSM_FP32C_LEARNED, blob)
-    # every root meets the same 1e-10 residual tolerance, so the paths agree far
-    # below the 1e-4 accuracy bar of the FP32 forms
-    assert np.max(np.abs(xl - xp)) < 1e-8
+    # every root passes the same residual test: residual <= tol = 1e-10, or the FP32
+    # forms' stagnation rule, which accepts up to 64 tol.  The implicit map is strongly
+    # monotone (1 - h L_v ~ 1), so each step's roots of the two runs differ by at most
+    # 2 x 64 tol, and over K steps by about K x 2 x 64 tol = 3.1e-7 (growth over T =
+    # 3/32 is a few percent): far below the 1e-4 accuracy bar of the FP32 forms
+    assert np.max(np.abs(xl - xp)) < 4e-7
     rows_plain, rows_learned = sp["newton_rows"] / K, sl["newton_rows"] / K
     print("pair rows per step: plain %.0f, learned %.0f (%.2fx); fallbacks %d"
           % (rows_plain, rows_learned, rows_plain / rows_learned, sl["fallbacks"]))
