@@ -55,3 +55,28 @@ def contraction_curve(gamma, h, T, x0, z0, N=1000, seed=0, precision=SSM_FP64):
     a.close()
     b.close()
     return np.arange(M + 1) * h, np.array(out)
+
+
+def gamma_sweep(gammas=(-12.0, -8.0, -4.0, 0.0, 2.0, 4.0, 6.0, 8.0, 12.0), h=0.1, T=3.0, N=1000, seed=0):
+    """The §3.4.2 experiment at the paper's step h = 0.1: for each gamma, beta of the
+    stability theorem and, from two runs X_0 = 1, Z_0 = 5 on the same Brownian paths,
+    the observed mean-square contraction factor per step
+    ((1/N) sum |X_M - Z_M|^2 / |1 - 5|^2)^(1/M), next to the theorem's 1 + beta h
+    (a bound where theorem_applies, i.e. 1 - h (2 L_v + 1) > 0, and beta < 0),
+    and E|X_T|^2 from X_0 = 1.  Returns a list of dicts."""
+    out = []
+    for g in gammas:
+        b = beta(h, **glstab_constants(g))
+        t, d2 = contraction_curve(g, h, T, 1.0, 5.0, N=N, seed=seed)
+        _, m2 = second_moment_curve(g, h, T, N=N, x0=1.0, seed=seed)
+        M = t.size - 1
+        k = glstab_constants(g)
+        out.append(dict(gamma=g, beta=b, theorem_applies=bool(1.0 - h * (2.0 * k["Lv"] + 1.0) > 0.0),
+                        theorem_factor=1.0 + b * h, observed_factor=float((d2[-1] / d2[0]) ** (1.0 / M)),
+                        m2_T=float(m2[-1])))
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    print(json.dumps(gamma_sweep()))

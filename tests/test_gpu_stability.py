@@ -72,3 +72,21 @@ def test_second_moment_decays(S, h):
     assert m2[0] == pytest.approx(1.0)
     assert m2[-1] < 0.05
     assert np.all(m2[1:] < m2[0])
+
+
+def test_gamma_sweep_at_the_papers_step(S):
+    """§3.4.2 at h = 0.1: where the theorem applies (1 - h (2 L_v + 1) > 0) and gives
+    beta < 0 (gamma = 0 here) the observed mean-square contraction factor per step is
+    within 1 + beta h; the factor grows with gamma (the gamma-split moves the linear
+    damping from the implicit v to the explicit b: per step the difference of two runs
+    scales by about (1 + h gamma) / (1 + h (5/2 + gamma)), increasing in gamma)."""
+    from paper_2105_09688_gb300 import stability as st
+    rows = st.gamma_sweep(gammas=(-8.0, -4.0, 0.0, 4.0, 8.0), T=2.0, N=500, seed=85)
+    checked = 0
+    for r in rows:
+        if r["theorem_applies"] and r["beta"] < 0:
+            assert r["observed_factor"] <= r["theorem_factor"] * (1 + 1e-9), r
+            checked += 1
+    assert checked >= 1
+    f = [r["observed_factor"] for r in rows]
+    assert all(f[k] <= f[k + 1] for k in range(len(f) - 1)), rows
