@@ -75,7 +75,10 @@ def parse():
     p.add_argument("--batched", type=int, default=1, help="also time the 64-ensemble batched form (1/0)")
     p.add_argument("--o-n", type=int, default=1, help="also time the O(N) kernels at N=2^26 against HBM (1/0)")
     p.add_argument("--profile-o-n", type=int, default=0, metavar="LOG2N",
-                   help="profiling driver: 4 OU steps (d=3) at N = 2^LOG2N in the form of --precision, and exit")
+                   help="profiling driver: 4 steps of the O(N) coefficient set --profile-set at N = 2^LOG2N in "
+                        "the form of --precision, and exit")
+    p.add_argument("--profile-set", default="ou", choices=["ou", "gl1", "gl2", "poly", "cs"],
+                   help="--profile-o-n: OU (d = 3) or one of the moment-interaction examples")
     p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
@@ -107,13 +110,18 @@ def profile_kernels(args):
 
 
 def profile_o_n(args):
-    """Small, self-terminating case for ncu: four OU steps of the O(N) kernels."""
+    """Small, self-terminating case for ncu: four steps of the O(N) kernels."""
     from paper_2105_09688_gb300 import build as B
     B.build()
     import paper_2105_09688_gb300 as S
     prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
-    s = S.SSM(d=ON_D, N=1 << args.profile_o_n, h=2.0 ** -6, T=1.0, coef=S.SSM_COEF_OU, seed=7, precision=prec,
-              coef_params=(-1.0, 0.5, 0.5), x0_mean=1.0, x0_std=0.5)
+    if args.profile_set == "ou":
+        d, coef, p, m0, s0 = ON_D, S.SSM_COEF_OU, (-1.0, 0.5, 0.5), 1.0, 0.5
+    else:
+        d, cname, p, m0, s0 = MOMENT_MODELS[args.profile_set]
+        coef = getattr(S, cname)
+    s = S.SSM(d=d, N=1 << args.profile_o_n, h=2.0 ** -6, T=1.0, coef=coef, seed=7, precision=prec,
+              coef_params=p, x0_mean=m0, x0_std=s0)
     s.run_steps(4)
     s.sync()
     s.close()
@@ -244,6 +252,12 @@ def bench_batched(torch, S, stream):
 
 
 ON_LOG2N, ON_D = 26, 3
+# The paper's moment-interaction examples timed beside OU: name -> (d, coefficient set,
+# parameters, X_0 mean, X_0 standard deviation).
+MOMENT_MODELS = {"gl1": (1, "SSM_COEF_GL1", (1.5, 0.5), 1.0, 0.0),
+                 "gl2": (1, "SSM_COEF_GL2", (1.5, 0.5), 1.0, 0.0),
+                 "poly": (1, "SSM_COEF_POLY", (-1.0,), 1.0, 0.0),
+                 "cs": (2, "SSM_COEF_CS", (2.0, 4.0), 1.0, 2.0 ** 0.5)}
 ON_BYTES_PER_PARTICLE_STEP = 4 * 8 * ON_D   # implicit step: read X, write Y; step 2: read Y, write X (FP64)
 
 
@@ -290,10 +304,8 @@ def bench_o_n(torch, S, stream, steps=5, warmup=3):
         s.close()
     # the paper's moment-interaction examples, FP32C, same N (32 d bytes per particle-step)
     models = {}
-    for name, d, coef, p, m0, s0 in (("gl1", 1, S.SSM_COEF_GL1, (1.5, 0.5), 1.0, 0.0),
-                                     ("gl2", 1, S.SSM_COEF_GL2, (1.5, 0.5), 1.0, 0.0),
-                                     ("poly", 1, S.SSM_COEF_POLY, (-1.0,), 1.0, 0.0),
-                                     ("cs", 2, S.SSM_COEF_CS, (2.0, 4.0), 1.0, 2.0 ** 0.5)):
+    for name, (d, cname, p, m0, s0) in MOMENT_MODELS.items():
+        coef = getattr(S, cname)
         s = S.SSM(d=d, N=N, h=2.0 ** -6, T=1.0, coef=coef, seed=7, stream=stream, precision=S.SSM_FP32C,
                   coef_params=p, x0_mean=m0, x0_std=s0)
         s.run_steps(warmup)

@@ -128,23 +128,93 @@ __device__ __forceinline__ double cardano_root_a(double x, double h, double a) {
 }
 __device__ __forceinline__ double cardano_root(double x, double h) { return cardano_root_a(x, h, 1.0 - h); }
 
-// The root of h y^3 + a y = x for the FP32C forms: the same Cardano form in FP32
-// (relative error ~1e-6), then one Newton correction with the residual in FP64 and
-// the derivative in FP32, which leaves ~1e-13 relative (quadratic convergence, plus
-// the derivative's FP32 rounding times the first error), with five FP64 operations.
-template <bool A1>   // A1: a = 1 (a y then needs no FP64 multiply)
-__device__ __forceinline__ double cardano32_a(double x, double h, double a) {
-    const float xf = f64_to_f32(x), hf = (float)h, af = (float)a;
-    const float p3 = af / (3.0f * hf), q = -xf / hf;
-    const float disc = 0.25f * q * q + p3 * p3 * p3;
+// The root of h y^3 + a y = x + c for the FP32C forms (c: GL2's measure term, else
+// 0).  The Cardano form in FP32 gives y0 (relative error ~1e-7); one Newton
+// correction y0 - f(y0) / f'(y0) follows, with the residual f = h y0^3 + a y0 - x - c
+// evaluated in double-float arithmetic on the FP32 pipe (error-free products by FMA
+// and Knuth's two-sum; x split into two floats on the integer pipes, h, a and c
+// split once per thread) to ~2^-47 of its terms, and the derivative in FP32.  That
+// leaves ~1e-13 relative (quadratic convergence plus the derivative's rounding
+// times the first error; for |x| < 2^-74 the low half of x is dropped, < 2^-98
+// absolute).  One FP64 operation per root: the final add.
+struct Cubic32 {
+    float hf, af, p3, ih;           // h, a, a / (3 h), 1 / h in FP32
+    float h_hi, h_lo, a_hi, a_lo;   // h and a as unevaluated pairs of floats
+    float c_hi, c_lo;               // c likewise
+};
+__device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
+    hi = f64_to_f32(v);
+    lo = f64_to_f32(v - f32_to_f64(hi));
+}
+__device__ __forceinline__ Cubic32 make_cubic32(double h, double a, double c) {   // once per thread
+    Cubic32 k;
+    k.hf = (float)h;
+    k.af = (float)a;
+    k.p3 = (float)(a / (3.0 * h));
+    k.ih = (float)(1.0 / h);
+    split_pair(h, k.h_hi, k.h_lo);
+    split_pair(a, k.a_hi, k.a_lo);
+    split_pair(c, k.c_hi, k.c_lo);
+    return k;
+}
+// v = hi + lo with hi = v rounded to FP32 and lo = v - hi rounded to FP32, on the
+// integer pipes: the 29 bits that the rounding drops, or their complement when it
+// rounds up, scaled by the unit of v's last bit (lo = 0 for |v| < 2^-74 or > 2^179).
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
+    hi = f64_to_f32(v);
+    unsigned long long b;
+    memcpy(&b, &v, sizeof b);
+    const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+    const unsigned e = (bh >> 20) & 0x7ffu;
+    const unsigned m = ((bh & 0xfffffu) << 3) | (bl >> 29);
+    const unsigned rest = bl & 0x1fffffffu;
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));
+    const unsigned R = up ? 0x20000000u - rest : rest;
+    const float unit = __uint_as_float(((e - 948u) & 0xffu) << 23);                  // 2^(e - 1075)
+    const float mag = (e - 949u < 254u) ? u32_to_f32(R) * unit : 0.0f;
+    lo = __uint_as_float(__float_as_uint(mag) ^ (((bh >> 31) ^ (up ? 1u : 0u)) << 31));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+template <bool A1, bool SHIFT>   // A1: a = 1; SHIFT: c != 0
+__device__ __forceinline__ double cardano32_a(double x, const Cubic32 &k) {
+    float xh, xl;
+    split_f64(x, xh, xl);
+    const float xs = SHIFT ? xh + k.c_hi : xh;
+    const float q = -xs * k.ih;
+    const float disc = fmaf(0.25f * q, q, k.p3 * k.p3 * k.p3);
     float u = cbrtf(0.5f * fabsf(q) + sqrtf(disc));
     if (q > 0.0f) u = -u;
-    const float w = -p3 / u;
-    const float y0 = -q / (u * u + p3 + w * w);
-    const double yd = f32_to_f64(y0);
-    const double f = fma(h * yd, yd * yd, A1 ? yd : a * yd) - x;
-    const float fp = fmaf(3.0f * hf * y0, y0, af);
-    return yd - f32_to_f64(f64_to_f32(f) / fp);
+    const float w = __fdividef(-k.p3, u);
+    const float y0 = __fdividef(-q, fmaf(u, u, k.p3) + w * w);
+    // h y0^3 = r + rl
+    const float p = y0 * y0, ep = fmaf(y0, y0, -p);
+    const float cb = p * y0, ecb = fmaf(p, y0, -cb);
+    const float cl = fmaf(ep, y0, ecb);
+    const float r = k.h_hi * cb, er = fmaf(k.h_hi, cb, -r);
+    const float rl = fmaf(k.h_hi, cl, fmaf(k.h_lo, cb, er));
+    // a y0 = s + sl
+    float s = y0, sl = 0.0f;
+    if (!A1) {
+        s = k.a_hi * y0;
+        sl = fmaf(k.a_lo, y0, fmaf(k.a_hi, y0, -s));
+    }
+    // f = (s - x_hi - c_hi) + r + (small terms)
+    float t, te, v, ve;
+    two_sum(s, -xh, t, te);
+    float ce = 0.0f;
+    if (SHIFT) {
+        float t2;
+        two_sum(t, -k.c_hi, t2, ce);
+        t = t2;
+    }
+    two_sum(t, r, v, ve);
+    const float f = v + ((ve + te + ce) + (rl + sl - xl - (SHIFT ? k.c_lo : 0.0f)));
+    const float fp = fmaf(3.0f * k.hf * y0, y0, k.af);
+    return f32_to_f64(y0) - f32_to_f64(__fdividef(f, fp));
 }
 
 __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, int64_t n, double h) {
@@ -180,6 +250,7 @@ k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, in
     // the cubic h3 y^3 + a1 y = x + shift
     const double h3 = coef == SSM_COEF_GLSTAB ? 0.25 * h : h;
     const double a1 = coef == SSM_COEF_GLSTAB ? 1.0 + h * (2.5 + p0) : 1.0;
+    const Cubic32 k32 = make_cubic32(h3, a1, shift);
     auto add = [&](int c, double v) {
         if (F32) two_sum_acc(mh[c], ml[c], f64_to_f32(v));
         else m[c] += v;
@@ -194,8 +265,8 @@ k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, in
         auto root = [&](int c, double xv) -> double {
             if (LIN) return xv * lin;
             if (c > 0) return xv;   // X part of Cucker-Smale's (V, X): v = 0
-            const double xs = SHIFT ? xv + shift : xv;
-            return F32 ? cardano32_a<A1>(xs, h3, a1) : cardano_root_a(xs, h3, a1);
+            if (F32) return cardano32_a<A1, SHIFT>(xv, k32);
+            return cardano_root_a(SHIFT ? xv + shift : xv, h3, a1);
         };
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += 2 * stride) {
@@ -494,15 +565,17 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // FP32C form (F32): dW from the FP32 transform, the increment h b + sigma dW in FP32
 // added to the FP64 state with one FP64 add, and the moments from FP32 powers in
 // Kahan-compensated FP32 per thread (FP64 across threads and blocks).  FP64 form:
-// all FP64.  Compiled for EUL_MIN_BLOCKS resident blocks per SM and launched on
-// EUL_BLOCKS blocks, one wave.
+// all FP64.  Compiled for eul_min_blocks<D> resident blocks per SM (3 at d = 2 and
+// 3, whose FP32C forms need more than 64 registers a thread; 4 at d = 1) and
+// launched on that many blocks per SM, one wave.
 // FAM, the coefficient family, fixed at compile time so that each instance carries
 // only its own branch: EUL_PAIR (b from the pair partial sums, sigma per particle),
 // EUL_OU (b = lambda mean(Y), sigma = eta, the same for every particle), EUL_GEN
 // (the other moment sets: b and sigma from Y and its means, moment_b / moment_sigma).
 enum : int { EUL_PAIR = 0, EUL_OU = 1, EUL_GEN = 2 };
+template <int D> constexpr int eul_min_blocks = D >= 2 ? EUL_MIN_BLOCKS : RED_BLOCKS / 152;
 template <int D, bool F32, int FAM>
-__global__ void __launch_bounds__(EUL_THREADS, EUL_MIN_BLOCKS)
+__global__ void __launch_bounds__(EUL_THREADS, eul_min_blocks<D>)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
         double bscale, int coef, double p0, double p1, double p2, const double *__restrict__ ymean, int64_t N,
         int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
@@ -779,7 +852,7 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const bool f32 = c->prec != SSM_FP64;
     // families by dimension: d = 1 pair sets, OU, GL/POLY/GLSTAB; d = 2 OU, CS; d = 3 pair sets, OU
     const int fam = c->coef == SSM_COEF_OU ? EUL_OU : is_moment_set(c->coef) ? EUL_GEN : EUL_PAIR;
-#define SSM_EUL(D, F, G) k_euler<D, F, G><<<EUL_BLOCKS, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
+#define SSM_EUL(D, F, G) k_euler<D, F, G><<<eul_min_blocks<D> * 152, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
         c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, \
         c->ticket, c->mom, c->err, c->counters)
 #define SSM_EUL_G(D, G) { if (f32) SSM_EUL(D, true, G); else SSM_EUL(D, false, G); }

@@ -122,3 +122,39 @@ def test_fp32c_large_n_sampled_steps(S, name):
             xo = O.explicit_one(P, y, int(i), n)
             assert np.max(np.abs(x1[i] - xo)) < 1e-5 * max(1.0, np.abs(xo).max())
     s.close()
+
+
+@pytest.mark.parametrize("name,gamma", [("gl1", None), ("gl2", None), ("cs", None), ("glstab", 2.0)])
+def test_fp32c_cubic_roots_over_a_wide_range(S, name, gamma):
+    """Step 1 of the cubic sets in the FP32C form (FP32 Cardano root, one Newton
+    correction with the residual in double-float arithmetic) against the oracle's
+    root for states over 1e-30 .. 1e6 of both signs, every particle: within 1e-12
+    of the larger of |y| and |x| (absolute below 1e-15, where the dropped low half
+    of a state smaller than 2^-74 in magnitude is < 2^-98)."""
+    N = 4096
+    rng = np.random.default_rng(7)
+    if name == "glstab":
+        d, gcoef, ocoef, p = 1, S.SSM_COEF_GLSTAB, O.COEF_GLSTAB, (gamma,)
+    else:
+        d, gname, ocoef, p = SETS[name][0], SETS[name][1], SETS[name][2], SETS[name][3]
+        gcoef = getattr(S, gname)
+    x = np.zeros((N, d))
+    x[:, 0] = rng.choice([-1.0, 1.0], N) * 10.0 ** rng.uniform(-30, 6, N)
+    x[:8, 0] = [0.0, -0.0, 1.0, -1.0, 1e6, -1e6, 2.0 ** -74, 3.0]
+    if d == 2:
+        x[:, 1] = rng.standard_normal(N)
+    s = S.SSM(d=d, N=N, h=H, T=1.0, coef=gcoef, seed=63, precision=S.SSM_FP32C, coef_params=p, x0_mean=0.0,
+              x0_std=1.0)
+    s.set_state(x, 0)
+    s.step()
+    y = s.get_stage(S.SSM_STAGE_Y)
+    s.close()
+    # set_state recomputes the moments of the planted state in FP64, so GL2's measure
+    # term is the oracle's
+    P = O.problem(d=d, coef=ocoef, N=N, h=H, T=1.0, seed=63, p=p, x0_mean=0.0, x0_std=1.0)
+    yo, it, bad = O.implicit_step(P, x)
+    assert bad == 0
+    # relative to the larger of the root and the state: GL2's x + c is formed to
+    # ~2^-48 of its terms, which near a root y ~ 0 (x ~ -c) is large against |y|
+    err = np.abs(y - yo) / np.maximum(np.maximum(np.abs(yo), np.abs(x[:, :1])), 1e-15)
+    assert err.max() < 1e-12, (err.max(), x[np.argmax(err.max(axis=1))])
