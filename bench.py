@@ -38,14 +38,14 @@ FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
 # operations): step 1: 1 + 3 x 2 (q) + 3 x 2 + 1 = 14; drift: 3 x 2 + 3 x 2 + 1 = 13.
 FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
 FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
-# DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 8> at
+# DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 4> at
 # N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), valid only for the
 # kernel sources it was measured on (their SHA-256 below); otherwise the roofline's
 # traffic is null.
-MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 8, 1 << 18), "bytes": 13019648 + 2622720,
+MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18), "bytes": 14478848 + 50865408,
                     "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu",
                                 "paper_2105_09688_gb300/csrc/ssm_device.cuh"),
-                    "sha256": "da9ade1962c547d0ecca69de13596a5a751fdedd2e97b29ea408806bd36b35d4"}
+                    "sha256": "eb98717b9941e41f91d155dd3d8e7d77db2d25c14bc8360d84f5e767d5aa896f"}
 
 
 def measured_traffic(kernel, kind, threads, rpt, n):

@@ -157,28 +157,6 @@ __device__ __forceinline__ Cubic32 make_cubic32(double h, double a, double c) { 
     split_pair(c, k.c_hi, k.c_lo);
     return k;
 }
-// v = hi + lo with hi = v rounded to FP32 and lo = v - hi rounded to FP32, on the
-// integer pipes: the 29 bits that the rounding drops, or their complement when it
-// rounds up, scaled by the unit of v's last bit (lo = 0 for |v| < 2^-74 or > 2^179).
-__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
-    hi = f64_to_f32(v);
-    unsigned long long b;
-    memcpy(&b, &v, sizeof b);
-    const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
-    const unsigned e = (bh >> 20) & 0x7ffu;
-    const unsigned m = ((bh & 0xfffffu) << 3) | (bl >> 29);
-    const unsigned rest = bl & 0x1fffffffu;
-    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m & 1u));
-    const unsigned R = up ? 0x20000000u - rest : rest;
-    const float unit = __uint_as_float(((e - 948u) & 0xffu) << 23);                  // 2^(e - 1075)
-    const float mag = (e - 949u < 254u) ? u32_to_f32(R) * unit : 0.0f;
-    lo = __uint_as_float(__float_as_uint(mag) ^ (((bh >> 31) ^ (up ? 1u : 0u)) << 31));
-}
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
 template <bool A1, bool SHIFT>   // A1: a = 1; SHIFT: c != 0
 __device__ __forceinline__ double cardano32_a(double x, const Cubic32 &k) {
     float xh, xl;

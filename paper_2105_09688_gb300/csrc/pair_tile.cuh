@@ -269,21 +269,72 @@ __device__ __forceinline__ int64_t target_index(const int *__restrict__ act, int
     return t < ntgt ? (act ? (int64_t)act[t] : t) : 0;
 }
 
-template <int NC, int R2>
-__device__ __forceinline__ void fold_subtile(float2 (&acc)[R2][NC], float2 (&hi)[R2][NC], float2 (&lo)[R2][NC]) {
+// The two-sum compensation accumulators (hi, lo) of a thread's R2 x NC float2 sums,
+// folded once per SUB sources: in registers, or in shared memory (SMEM), where they
+// leave the registers to the inner loop's accumulators and targets (more resident
+// blocks).  Shared layout slot-major, hl[(2 slot + {0: hi, 1: lo}) THREADS + tid],
+// slot = (k NC + c) 2 + lane: a warp's accesses fall in distinct banks.
+template <int R2, int NC, int THREADS, bool SMEM> struct Comp;
+template <int R2, int NC, int THREADS> struct Comp<R2, NC, THREADS, false> {
+    float2 hi[R2][NC], lo[R2][NC];
+    __device__ __forceinline__ Comp(float *, int) {
 #pragma unroll
-    for (int k = 0; k < R2; ++k)
+        for (int k = 0; k < R2; ++k)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            two_sum_acc(hi[k][c].x, lo[k][c].x, acc[k][c].x);
-            two_sum_acc(hi[k][c].y, lo[k][c].y, acc[k][c].y);
-            acc[k][c] = f2(0.f, 0.f);
-        }
+            for (int c = 0; c < NC; ++c) { hi[k][c] = f2(0.f, 0.f); lo[k][c] = f2(0.f, 0.f); }
+    }
+    __device__ __forceinline__ void fold(float2 (&acc)[R2][NC]) {
+#pragma unroll
+        for (int k = 0; k < R2; ++k)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                two_sum_acc(hi[k][c].x, lo[k][c].x, acc[k][c].x);
+                two_sum_acc(hi[k][c].y, lo[k][c].y, acc[k][c].y);
+                acc[k][c] = f2(0.f, 0.f);
+            }
+    }
+    __device__ __forceinline__ double value(int k, int c, int e) const {
+        return e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
+    }
+};
+template <int R2, int NC, int THREADS> struct Comp<R2, NC, THREADS, true> {
+    float *my;   // this thread's column: constant offsets from one base
+    __device__ __forceinline__ Comp(float *p, int t) : my(p + t) {
+#pragma unroll
+        for (int s = 0; s < 4 * R2 * NC; ++s) my[s * THREADS] = 0.f;
+    }
+    __device__ __forceinline__ void acc1(int slot, float a) {
+        float h = my[(2 * slot) * THREADS], l = my[(2 * slot + 1) * THREADS];
+        two_sum_acc(h, l, a);
+        my[(2 * slot) * THREADS] = h;
+        my[(2 * slot + 1) * THREADS] = l;
+    }
+    __device__ __forceinline__ void fold(float2 (&acc)[R2][NC]) {
+#pragma unroll
+        for (int k = 0; k < R2; ++k)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                acc1((k * NC + c) * 2 + 0, acc[k][c].x);
+                acc1((k * NC + c) * 2 + 1, acc[k][c].y);
+                acc[k][c] = f2(0.f, 0.f);
+            }
+    }
+    __device__ __forceinline__ double value(int k, int c, int e) const {
+        const int slot = (k * NC + c) * 2 + e;
+        return (double)my[(2 * slot) * THREADS] + (double)my[(2 * slot + 1) * THREADS];
+    }
+};
+// Compensation in shared memory for the shapes of 4 targets a thread, where it was
+// measured faster (128 x 4 at N = 2^18: step-1 pass 20.65 ms against 21.16 ms with
+// it in registers); with 8 targets a thread it was slower (21.9 against 21.0 ms),
+// so those keep it in registers.  At most 32 KB beside the source sub-tile.
+__host__ __device__ constexpr bool comp_in_smem(int threads, int r) {
+    return r <= 4 && threads * (r / 2) * 4 * 4 * 4 <= 32768;
 }
 
 // Difference form of a packed tile (buf: 2*SUB float4 of shared memory).
 template <int KIND, int THREADS, int R>
-__device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_one, const double *__restrict__ src,
+__device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                  const double *__restrict__ tgt, const int *__restrict__ act,
                                                  int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
                                                  double scale, double *__restrict__ part) {
@@ -307,11 +358,12 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_on
         nty[k] = f2(v[0][1], v[1][1]);
         ntz[k] = f2(v[0][2], v[1][2]);
     }
-    float2 acc[R2][NC], hi[R2][NC], lo[R2][NC];
+    float2 acc[R2][NC];
 #pragma unroll
     for (int k = 0; k < R2; ++k)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) { acc[k][c] = f2(0.f, 0.f); hi[k][c] = f2(0.f, 0.f); lo[k][c] = f2(0.f, 0.f); }
+        for (int c = 0; c < NC; ++c) acc[k][c] = f2(0.f, 0.f);
+    Comp<R2, NC, THREADS, comp_in_smem(THREADS, R)> comp(hl, tid);
 
     for (int64_t base = j0; base < j1; base += SUB) {
         const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
@@ -342,7 +394,7 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_on
                     pair2<KIND>(f2(a.x, a.y), f2(a.z, a.w), b, ntx[k], nty[k], ntz[k], one, acc[k]);
             }
         }
-        fold_subtile<NC, R2>(acc, hi, lo);
+        comp.fold(acc);
     }
 #pragma unroll
     for (int k = 0; k < R2; ++k)
@@ -351,9 +403,7 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_on
             const int64_t t = t0 + (2 * k + e) * THREADS + tid;
             if (t < ntgt) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    part[(int64_t)c * Np + t] =
-                        e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
+                for (int c = 0; c < NC; ++c) part[(int64_t)c * Np + t] = comp.value(k, c, e);
             }
         }
 }
@@ -365,7 +415,7 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, const float2 *s_on
 //           applies (the linear t_i term is taken in FP64 here);
 //   drift : sum_j e_ij (s_j - t_i) in scaled units, t_i = scale (y_i - c) exact.
 template <int KIND, int THREADS, int R>
-__device__ __forceinline__ void tile_packed_exp(float4 *buf, const float2 *s_one, const double *__restrict__ src,
+__device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                 const double *__restrict__ tgt, const int *__restrict__ act,
                                                 int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
                                                 double scale, const double (&cc)[3], double *__restrict__ part) {
@@ -393,11 +443,12 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, const float2 *s_one
         uz[k] = f2(v[0][2], v[1][2]);
         kb[k] = f2(v[0][3], v[1][3]);
     }
-    float2 acc[R2][NX], hi[R2][NX], lo[R2][NX];
+    float2 acc[R2][NX];
 #pragma unroll
     for (int k = 0; k < R2; ++k)
 #pragma unroll
-        for (int c = 0; c < NX; ++c) { acc[k][c] = f2(0.f, 0.f); hi[k][c] = f2(0.f, 0.f); lo[k][c] = f2(0.f, 0.f); }
+        for (int c = 0; c < NX; ++c) acc[k][c] = f2(0.f, 0.f);
+    Comp<R2, NX, THREADS, comp_in_smem(THREADS, R)> comp(hl, tid);
 
     for (int64_t base = j0; base < j1; base += SUB) {
         const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
@@ -431,7 +482,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, const float2 *s_one
                                  one, acc[k]);
             }
         }
-        fold_subtile<NX, R2>(acc, hi, lo);
+        comp.fold(acc);
     }
 #pragma unroll
     for (int k = 0; k < R2; ++k)
@@ -442,8 +493,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, const float2 *s_one
                 const int64_t i = act ? (int64_t)act[t] : t;
                 double S[NX];
 #pragma unroll
-                for (int c = 0; c < NX; ++c)
-                    S[c] = e == 0 ? (double)hi[k][c].x + (double)lo[k][c].x : (double)hi[k][c].y + (double)lo[k][c].y;
+                for (int c = 0; c < NX; ++c) S[c] = comp.value(k, c, e);
                 if (NEWTON) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -485,6 +535,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
     static_assert(R % 2 == 0, "targets per thread come in pairs");
     static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
     __shared__ float4 buf[2 * SUB];
+    __shared__ float s_hl[comp_in_smem(THREADS, R) ? THREADS * (R / 2) * 4 * 4 : 1];
     __shared__ float2 s_one;
     __shared__ double s_red[THREADS / 32][4];
     const int tid = threadIdx.x;
@@ -531,11 +582,11 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
             }
         }
         if (__syncthreads_and(ok)) {
-            tile_packed_exp<KIND, THREADS, R>(buf, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part);
+            tile_packed_exp<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part);
             return;
         }
     }
-    tile_packed_diff<KIND, THREADS, R>(buf, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, part);
+    tile_packed_diff<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, part);
 }
 
 }  // namespace ssm
