@@ -88,7 +88,7 @@ def test_outliers_fall_back_per_block(S):
     x0[0] = (20.0, -3.0, 5.0)
     x0[1777] = (0.0, 0.0, 12.0)
     x0[2999] = (-9.0, 0.0, 0.0)
-    for shape in [(2, 128, 8), (1, 128, 8)]:
+    for shape in [(2, 128, 8), (2, 128, 4), (1, 128, 8)]:
         s = _ctx(S, N, seed, shape)
         s.set_state(x0, 0)
         _check_one_step(S, s, P)
@@ -109,10 +109,13 @@ def test_cloud_far_from_origin(S):
     s.close()
 
 
-def test_full_horizon_tolerances(S):
-    """N = 1536, h = 2^-8, T = 1 with the expansion in both pair kinds."""
+@pytest.mark.parametrize("step1_rpt", [8, 4])
+def test_full_horizon_tolerances(S, step1_rpt):
+    """N = 1536, h = 2^-8, T = 1 with the expansion in both pair kinds (drift 128 x 8;
+    step-1 sums 128 x 8, or 128 x 4 with the accumulators in shared memory)."""
     N, seed = 1536, 2
     s = _ctx(S, N, seed, (2, 128, 8))
+    s.set_plan(0, 2, 128, step1_rpt)
     s.run()
     x, n = s.get_state()
     m = s.moments()

@@ -266,6 +266,24 @@ def test_coupled3d_full_size_sampled_fp32c(S):
     s.close()
 
 
+@pytest.mark.parametrize("learned", [False, True])
+def test_coupled3d_full_size_sampled_bench_configuration(S, learned):
+    """N = 2^18, h = 2^-8, seed 2 in the launch configuration the benchmark times:
+    step-1 sums on the packed expansion with 128 threads x 4 targets (two-sum
+    accumulators in shared memory), the drift with 128 x 8, plain FP32C and the
+    learned form (the shipped network): one step, sampled."""
+    N, h = 1 << 18, 2.0 ** -8
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2,
+              precision=S.SSM_FP32C_LEARNED if learned else S.SSM_FP32C)
+    if learned:
+        S.load_ws(s)
+    s.set_plan(0, 2, 128, 4)
+    s.set_plan(1, 2, 128, 8)
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=2)
+    _sampled_step_check(S, s, P, 24, 2e-9, 6e-7)
+    s.close()
+
+
 def test_coupled3d_full_size_sampled_fp64(S):
     """N = 2^18 in FP64: one step, sampled, 1e-10 relative."""
     N, h = 1 << 18, 2.0 ** -8
