@@ -173,3 +173,23 @@ def test_batch_set_plan_rejects_unknown_shape(S):
     with pytest.raises(S.SSMError):
         f.set_plan(2, 8, 8, 4096)
     f.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 33, 129, 513])
+def test_tiny_and_ragged_n_in_the_benchmark_shapes(S, N):
+    """Degenerate and ragged sizes in the benchmark's shapes (step-1 sums 128 x 4,
+    drift 128 x 8; one partly filled tile, N = 1 a single self-interacting
+    particle), with T = h (a one-step horizon): Y and b of the step against the
+    oracle, and no step past the horizon."""
+    seed = 24
+    s = S.SSM(d=3, N=N, h=H, T=H, coef=S.SSM_COEF_COUPLED3D, seed=seed, precision=S.SSM_FP32C)
+    s.set_plan(0, 2, 128, 4)
+    s.set_plan(1, 2, 128, 8)
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=H, T=H, seed=seed)
+    _check_one_step(S, s, P)
+    x, n = s.get_state()
+    assert n == 1 and np.all(np.isfinite(x))
+    with pytest.raises(S.SSMError) as e:
+        s.step()
+    assert e.value.status == S.SSM_ESTATE
+    s.close()
