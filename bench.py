@@ -82,6 +82,11 @@ def parse():
     p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
+    p.add_argument("--measure-y", type=int, default=0, choices=[0, 1],
+                   help="--profile-kernels: step 1 against mu^Y (one step, no isolated passes)")
+    p.add_argument("--profile-batched", type=int, default=0, metavar="K",
+                   help="profiling driver: the 64-ensemble batched workload over T = 2^-K (FP32C, one graph "
+                        "launch), and exit")
     p.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"], help="form for --profile-kernels")
     p.add_argument("--packed", type=int, default=0, choices=[0, 1, 2],
                    help="--profile-kernels: pair-kernel form (0 scalar, 1 packed difference form, 2 packed "
@@ -98,15 +103,32 @@ def profile_kernels(args):
     B.build()
     import paper_2105_09688_gb300 as S
     prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
-    s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec)
+    s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec,
+              measure_y=args.measure_y)
     if args.packed:
         s.set_plan(0, args.packed, 128, args.rpt)
         s.set_plan(1, args.packed, 128, args.rpt)
     s.step()
-    s.pair_pass(0)
-    s.pair_pass(1)
+    if not args.measure_y:
+        s.pair_pass(0)
+        s.pair_pass(1)
     s.sync()
     s.close()
+
+
+def profile_batched(args):
+    """Small, self-terminating case for ncu: the batched workload's 64 ensembles over
+    a shortened horizon T = 2^-K (their own N and h), one graph launch."""
+    from paper_2105_09688_gb300 import build as B
+    B.build()
+    import paper_2105_09688_gb300 as S
+    from paper_2105_09688_gb300.convergence import mixed_ensembles
+    T = 2.0 ** -args.profile_batched
+    descs = [dict(d, T=T) for d in mixed_ensembles() if d["h"] <= T]
+    b = S.Batch(descs, precision=S.SSM_FP32C)
+    b.run()
+    b.sync()
+    b.close()
 
 
 def profile_o_n(args):
@@ -356,6 +378,9 @@ def main():
         return
     if args.profile_o_n:
         profile_o_n(args)
+        return
+    if args.profile_batched:
+        profile_batched(args)
         return
     import torch
     if world > 1:

@@ -294,13 +294,18 @@ k_train_bwd(const float *__restrict__ blob, int B, const float *__restrict__ Z, 
     }
 }
 
-// Gradient of every parameter, summed over the batch in sample order (one
-// thread per parameter; deterministic).
+// Gradient of every parameter over the batch, in two deterministic stages: block
+// (x, c) sums samples [c Bc, (c + 1) Bc) of its 128 parameters in sample order
+// into part[c][p] (one thread per parameter and chunk, WG_CHUNKS chunks: enough
+// blocks to fill the device), then k_train_wgrad_sum adds the chunks in order.
+constexpr int WG_CHUNKS = 64;
 __global__ void __launch_bounds__(128)
 k_train_wgrad(int B, const float *__restrict__ FZ, const float *__restrict__ A, const float *__restrict__ D,
-              float *__restrict__ grad) {
+              float *__restrict__ part) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NPARAM) return;
+    const int bc = (B + WG_CHUNKS - 1) / WG_CHUNKS;
+    const int b0 = blockIdx.y * bc, b1 = b0 + bc < B ? b0 + bc : B;
     constexpr int DS = 3 * NH + NO;
     int dj, in_k = -1, in_layer = -1;   // delta column, input column (-1: bias), input kind
     if (p < P_B1) { dj = (p - P_W1) / NI; in_k = (p - P_W1) % NI; in_layer = 0; }
@@ -312,14 +317,26 @@ k_train_wgrad(int B, const float *__restrict__ FZ, const float *__restrict__ A, 
     else if (p < P_B4) { dj = 3 * NH + (p - P_W4) / NH; in_k = (p - P_W4) % NH; in_layer = 3; }
     else { dj = 3 * NH + (p - P_B4); }
     float s = 0.f;
-    for (int b = 0; b < B; ++b) {
+    for (int b = b0; b < b1; ++b) {
         const float dv = D[(int64_t)b * DS + dj];
         float av = 1.0f;
         if (in_layer == 0) av = FZ[(int64_t)b * NI + in_k];
         else if (in_layer > 0) av = A[(int64_t)b * 3 * NH + (in_layer - 1) * NH + in_k];
         s = fmaf(dv, av, s);
     }
+    part[(int64_t)blockIdx.y * NPARAM + p] = s;
+}
+__global__ void k_train_wgrad_sum(const float *__restrict__ part, float *__restrict__ grad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NPARAM) return;
+    float s = 0.f;
+    for (int c = 0; c < WG_CHUNKS; ++c) s += part[(int64_t)c * NPARAM + p];
     grad[p] = s;
+}
+static cudaError_t launch_wgrad(int B, const float *fz, const float *a, const float *d, float *part, float *grad) {
+    k_train_wgrad<<<dim3((NPARAM + 127) / 128, WG_CHUNKS), 128>>>(B, fz, a, d, part);
+    k_train_wgrad_sum<<<(NPARAM + 127) / 128, 128>>>(part, grad);
+    return cudaGetLastError();
 }
 
 // Adam on the FP32 master weights; writes the BF16-rounded blob used by the forward.
@@ -498,7 +515,7 @@ ssm_status ssm_ws_predict(const void *blob, size_t bytes, const float *feat, int
 ssm_status ssm_ws_grad(const void *blob, size_t bytes, const float *feat, const float *label, int64_t n,
                        float *grad, double *loss) {
     if (!blob_ok(blob, bytes) || !feat || !label || !grad || n < 1 || n > (1 << 20)) return SSM_EINVAL;
-    DevBuf db, df, dl, fz, z, a, d, g, ls;
+    DevBuf db, df, dl, fz, z, a, d, g, gp, ls;
     const int B = (int)n;
     cudaError_t e = set_smem_limits();
     if (e == cudaSuccess) e = db.alloc(BLOB_BYTES);
@@ -509,6 +526,7 @@ ssm_status ssm_ws_grad(const void *blob, size_t bytes, const float *feat, const 
     if (e == cudaSuccess) e = a.alloc(sizeof(float) * 3 * NH * n);
     if (e == cudaSuccess) e = d.alloc(sizeof(float) * (3 * NH + NO) * n);
     if (e == cudaSuccess) e = g.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = gp.alloc(sizeof(float) * NPARAM * WG_CHUNKS);
     if (e == cudaSuccess) e = ls.alloc(sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(db.p, blob, BLOB_BYTES, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(df.p, feat, sizeof(float) * NI * n, cudaMemcpyHostToDevice);
@@ -519,7 +537,7 @@ ssm_status ssm_ws_grad(const void *blob, size_t bytes, const float *feat, const 
         k_train_fwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), df.as<float>(), dl.as<float>(), nullptr, 0, B,
                                                fz.as<float>(), z.as<float>(), a.as<float>(), d.as<float>(), ls.as<double>());
         k_train_bwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), B, z.as<float>(), d.as<float>());
-        k_train_wgrad<<<(NPARAM + 127) / 128, 128>>>(B, fz.as<float>(), a.as<float>(), d.as<float>(), g.as<float>());
+        launch_wgrad(B, fz.as<float>(), a.as<float>(), d.as<float>(), gp.as<float>(), g.as<float>());
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(grad, g.p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost);
@@ -567,7 +585,7 @@ ssm_status ssm_ws_train(const float *feat, const float *label, int64_t n, int ep
     pack_blob(w, fm, fs, ym, ys, blob);
 
     const int B = batch;
-    DevBuf db, df, dl, dperm, fz, z, a, d, g, m, v, dw, ls;
+    DevBuf db, df, dl, dperm, fz, z, a, d, g, gp, m, v, dw, ls;
     cudaError_t e = set_smem_limits();
     if (e == cudaSuccess) e = db.alloc(BLOB_BYTES);
     if (e == cudaSuccess) e = df.alloc(sizeof(float) * NI * n);
@@ -578,6 +596,7 @@ ssm_status ssm_ws_train(const float *feat, const float *label, int64_t n, int ep
     if (e == cudaSuccess) e = a.alloc(sizeof(float) * 3 * NH * B);
     if (e == cudaSuccess) e = d.alloc(sizeof(float) * (3 * NH + NO) * B);
     if (e == cudaSuccess) e = g.alloc(sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = gp.alloc(sizeof(float) * NPARAM * WG_CHUNKS);
     if (e == cudaSuccess) e = m.alloc(sizeof(float) * NPARAM);
     if (e == cudaSuccess) e = v.alloc(sizeof(float) * NPARAM);
     if (e == cudaSuccess) e = dw.alloc(sizeof(float) * NPARAM);
@@ -610,7 +629,7 @@ ssm_status ssm_ws_train(const float *feat, const float *label, int64_t n, int ep
                                                    bi * Bl, Bl, fz.as<float>(), z.as<float>(), a.as<float>(),
                                                    d.as<float>(), ls.as<double>());
             k_train_bwd<<<blocks, 128, NET_SMEM>>>(db.as<float>(), Bl, z.as<float>(), d.as<float>());
-            k_train_wgrad<<<(NPARAM + 127) / 128, 128>>>(Bl, fz.as<float>(), a.as<float>(), d.as<float>(), g.as<float>());
+            launch_wgrad(Bl, fz.as<float>(), a.as<float>(), d.as<float>(), gp.as<float>(), g.as<float>());
             k_adam<<<(NPARAM + 127) / 128, 128>>>(g.as<float>(), m.as<float>(), v.as<float>(), dw.as<float>(),
                                                   db.as<float>(), lr_t, c1, c2);
             e = cudaGetLastError();
