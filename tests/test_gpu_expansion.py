@@ -135,10 +135,14 @@ DESCS = [dict(d=3, N=700, h=2.0 ** -5, T=0.25, seed=1200),
          dict(d=3, N=2100, h=2.0 ** -6, T=0.25, seed=1202)]
 
 
-def test_batch_expansion_matches_single_contexts(S):
+@pytest.mark.parametrize("r3", [8, 4])
+def test_batch_expansion_matches_single_contexts(S, r3):
+    """The batched expansion (d = 3 tiles of 8 targets a thread, accumulators in
+    registers, or of 4 with them in shared memory, the shape the batched benchmark's
+    autotuner picks) against single contexts and the batched difference form."""
     b = S.Batch(DESCS, precision=S.SSM_FP32C)
-    b.set_plan(2, 8, 8, 4096)
-    assert b.plan()["form"] == 2 and b.plan()["targets_per_thread_d3"] == 8
+    b.set_plan(2, 8, r3, 4096)
+    assert b.plan()["form"] == 2 and b.plan()["targets_per_thread_d3"] == r3
     b.run()
     c = S.Batch(DESCS, precision=S.SSM_FP32C)
     c.set_plan(1, 8, 8, 4096)
