@@ -65,7 +65,8 @@ def batch_study(descs, ref_log2=14, precision=SSM_FP32C, stream=None):
 
     Returns dict(per_ensemble=[dict(e, d, N, h, weak, strong)], by_h={h: (geometric
     mean weak, geometric mean strong)}, weak_slope, strong_slope, particle_steps);
-    the slopes are least-squares fits of log2 error against log2 h over all ensembles."""
+    the slopes are least-squares fits of log2 error against log2 h over all ensembles
+    (None with a single step size)."""
     runs = []
     for dsc in descs:
         if dsc["h"] <= dsc["T"] * 2.0 ** -ref_log2:
@@ -96,7 +97,10 @@ def batch_study(descs, ref_log2=14, precision=SSM_FP32C, stream=None):
         rows = [r for r in per if r["h"] == h]
         by_h[h] = tuple(float(2.0 ** np.mean(np.log2([max(r[k], 1e-300) for r in rows]))) for k in ("weak", "strong"))
     lh = np.log2([r["h"] for r in per])
-    slope = {k: float(np.polyfit(lh, np.log2([max(r[k], 1e-300) for r in per]), 1)[0]) for k in ("weak", "strong")}
+    if len(set(lh)) > 1:
+        slope = {k: float(np.polyfit(lh, np.log2([max(r[k], 1e-300) for r in per]), 1)[0]) for k in ("weak", "strong")}
+    else:   # a single step size: no rate
+        slope = {"weak": None, "strong": None}
     steps = sum(r["N"] * round(r["T"] / r["h"]) for r in runs)
     return dict(per_ensemble=per, by_h=by_h, weak_slope=slope["weak"], strong_slope=slope["strong"],
                 particle_steps=steps)

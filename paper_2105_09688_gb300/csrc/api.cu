@@ -129,7 +129,7 @@ Plan make_plan_shape(int64_t N, int kind, int vec2, int threads, int rpt, int fo
 // Default shape before any tuning: scalar kernels, 128 threads, 4 (FP32 d=3),
 // 8 (FP32 d=1) or 2 (FP64) targets per thread; chunks from the device's slots.
 Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
-    const int th = 128, r = fp32 ? (kind == PK_DRIFT1 ? 8 : 4) : 2;
+    const int th = 128, r = fp32 ? ((kind == PK_DRIFT1 || kind == PK_NEWTON1) ? 8 : 4) : 2;
     return make_plan_shape(N, kind, 0, th, r, force_chunks, device_slots(kind, fp32, 0, th, r));
 }
 

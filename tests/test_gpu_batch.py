@@ -144,8 +144,16 @@ def test_partial_runs_and_autotune(S):
     assert plan["chunk_len"] in (4096, 8192, 16384)
     b.run()
     for e in range(2):
-        assert b.get_state(e)[1] == round(1.0 / descs[e]["h"])
-        assert np.max(np.abs(b.get_state(e)[0] - xa[e])) < 1e-8
+        d = descs[e]
+        K = round(1.0 / d["h"])
+        assert b.get_state(e)[1] == K
+        # the tuned shapes sum the pair terms in another order (and, with 8 d = 1
+        # targets a thread, take one reciprocal in eight on the FMA pipe), so the two
+        # runs agree to what the FP32 forms' residual test admits: each root within
+        # 64 tol of the exact one (the stagnation rule), tol = 2^-27 h (1 + 64/sqrt(N)),
+        # so K steps differ by at most K x 2 x 64 tol
+        tol = max(1e-10, 2.0 ** -27 * d["h"] * (1.0 + 64.0 / math.sqrt(d["N"])))
+        assert np.max(np.abs(b.get_state(e)[0] - xa[e])) < K * 2 * 64 * tol
     a.close()
     b.close()
 
