@@ -39,27 +39,30 @@ FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
 FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
 FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
 # DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 4> at
-# N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), valid only for the
-# kernel sources it was measured on (their SHA-256 below); otherwise the roofline's
-# traffic is null.
-MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18), "bytes": 13517312 + 50745600,
+# N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), for each source-chunk
+# count the autotuner can pick for that shape (the partial sums written grow with it);
+# valid only for the kernel sources they were measured on (their SHA-256 below),
+# otherwise the roofline's traffic is null.
+MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18),
+                    "bytes_by_chunks": {13: 13517312 + 50745600, 19: 13830144 + 100968704,
+                                        26: 13951232 + 159262208, 32: 13766656 + 209635840},
                     "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu",
                                 "paper_2105_09688_gb300/csrc/ssm_device.cuh"),
                     "sha256": "152ddbd136becd299aa33636932feb5b8847db8d46b32f224ccfa23c237f9648"}
 
 
-def measured_traffic(kernel, kind, threads, rpt, n):
+def measured_traffic(kernel, kind, threads, rpt, n, chunks):
     """The ncu DRAM bytes per launch of this kernel if they were measured on the
     current sources, else None."""
     import hashlib
     m = MEASURED_TRAFFIC
-    if (kernel, kind, threads, rpt, n) != m["kernel"]:
+    if (kernel, kind, threads, rpt, n) != m["kernel"] or chunks not in m["bytes_by_chunks"]:
         return None
     h = hashlib.sha256()
     for f in m["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return m["bytes"] if h.hexdigest() == m["sha256"] else None
+    return m["bytes_by_chunks"][chunks] if h.hexdigest() == m["sha256"] else None
 METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
 
 
@@ -82,6 +85,8 @@ def parse():
     p.add_argument("--profile-kernels", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: one SSM step at N = 2^LOG2N, then one step-1 pair pass and one drift "
                         "pair pass (13 + 2 launches of k_pair), and exit")
+    p.add_argument("--chunks", type=int, default=0,
+                   help="--profile-kernels: source chunks of both pair kinds (0 = planned)")
     p.add_argument("--measure-y", type=int, default=0, choices=[0, 1],
                    help="--profile-kernels: step 1 against mu^Y (one step, no isolated passes)")
     p.add_argument("--profile-batched", type=int, default=0, metavar="K",
@@ -104,7 +109,7 @@ def profile_kernels(args):
     import paper_2105_09688_gb300 as S
     prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
     s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec,
-              measure_y=args.measure_y)
+              measure_y=args.measure_y, tile_chunks=args.chunks)
     if args.packed:
         s.set_plan(0, args.packed, 128, args.rpt)
         s.set_plan(1, args.packed, 128, args.rpt)
@@ -453,7 +458,7 @@ def main():
     dom_form = dom_plan["form"]
     executed = (FLOPS_PAIR_EXPANDED if dom_form == 2 else FLOPS_PAIR)[dom] * N_PART * N_PART / t_dom / 1e12
     traffic = measured_traffic(("k_pair", "k_pair2", "k_pair2x")[dom_form], dom, dom_plan["threads"],
-                               dom_plan["targets_per_thread"], N_PART)
+                               dom_plan["targets_per_thread"], N_PART, dom_plan["chunks"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
                 "kernel": "%s<%s> (%s)" % (("k_pair", "k_pair2", "k_pair2x")[dom_form],
