@@ -34,7 +34,7 @@ namespace ssm {
 
 template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
-template <> struct V4<double> { using t = double4; };
+template <> struct V4<double> { using t = double4_32a; };
 
 template <int KIND> struct KindInfo;
 template <> struct KindInfo<PK_DRIFT1> { static constexpr int D = 1, NC = 1; };
@@ -95,18 +95,18 @@ __device__ __forceinline__ void pair_newton1_fma(const float4 &s, float tx, floa
     acc[0] = fmaf(w, dx, acc[0]);
     acc[1] += w;
 }
-template <> __device__ __forceinline__ void pair<PK_DRIFT1, double>(const double4 &s, double tx, double, double, double *acc) {
+template <> __device__ __forceinline__ void pair<PK_DRIFT1, double>(const double4_32a &s, double tx, double, double, double *acc) {
     const double dx = s.x - tx;
     acc[0] += dx * exp(-(dx * dx));
 }
-template <> __device__ __forceinline__ void pair<PK_DRIFT3, double>(const double4 &s, double tx, double ty, double tz, double *acc) {
+template <> __device__ __forceinline__ void pair<PK_DRIFT3, double>(const double4_32a &s, double tx, double ty, double tz, double *acc) {
     const double dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
     const double e = exp(-(dx * dx + dy * dy + dz * dz) * 0.5);
     acc[0] += dx * e;
     acc[1] += dy * e;
     acc[2] += dz * e;
 }
-template <> __device__ __forceinline__ void pair<PK_NEWTON3, double>(const double4 &s, double tx, double ty, double tz, double *acc) {
+template <> __device__ __forceinline__ void pair<PK_NEWTON3, double>(const double4_32a &s, double tx, double ty, double tz, double *acc) {
     const double dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
     const double w = 1.0 / (1.0 + dx * dx + dy * dy + dz * dz);
     acc[0] += dx * w;
@@ -114,7 +114,7 @@ template <> __device__ __forceinline__ void pair<PK_NEWTON3, double>(const doubl
     acc[2] += dz * w;
     acc[3] += w;
 }
-template <> __device__ __forceinline__ void pair<PK_NEWTON1, double>(const double4 &s, double tx, double, double, double *acc) {
+template <> __device__ __forceinline__ void pair<PK_NEWTON1, double>(const double4_32a &s, double tx, double, double, double *acc) {
     const double dx = s.x - tx;
     const double w = 1.0 / (1.0 + dx * dx);
     acc[0] += dx * w;
@@ -494,7 +494,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         __syncthreads();
         const float2 one = *s_one;
         if (ns == SUB) {
-#pragma unroll 8
+#pragma unroll (NEWTON && R == 4 ? 16 : 8)   // timed: 128 x 4 step-1 pass 20.35 ms unrolled 16, 20.53 ms unrolled 8
             for (int s = 0; s < SUB; ++s) {
                 const float4 a = buf[2 * s], b = buf[2 * s + 1];
 #pragma unroll
