@@ -494,7 +494,9 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         __syncthreads();
         const float2 one = *s_one;
         if (ns == SUB) {
-#pragma unroll (NEWTON && R == 4 ? 16 : 8)   // timed: 128 x 4 step-1 pass 20.35 ms unrolled 16, 20.53 ms unrolled 8
+// unroll timed at N = 2^18: 128 x 4 step-1 pass 20.35 ms unrolled 16 (20.53 ms at 8);
+// 128 x 8 drift pass 17.50 ms unrolled 12 (17.67 ms at 8, 17.78 ms at 16)
+#pragma unroll (NEWTON && R == 4 ? 16 : (!NEWTON && R == 8) ? 12 : 8)
             for (int s = 0; s < SUB; ++s) {
                 const float4 a = buf[2 * s], b = buf[2 * s + 1];
 #pragma unroll
