@@ -256,9 +256,11 @@ ssm_status ssm_pair_pass(ssm_ctx *ctx, int which, int64_t *pairs);
  * runs are on 4 CPU cores): times every compiled shape (scalar or packed-FP32
  * kernel, threads per block, targets per thread; source chunks chosen to fill
  * whole waves of the device's resident-block slots) of each pair kind the
- * context uses, on its current state and stream, and keeps the fastest for
- * later steps.  best_ms (may be NULL) receives the best per-pass times
- * [step-1 sums, drift].  Synchronising; overwrites only the partial-sum scratch. */
+ * context uses, on its current state and stream, then 1.5, 2 and 2.5 times the
+ * chunk count of the fastest (unless ssm_opts.tile_chunks fixes it), and keeps
+ * the fastest for later steps.  best_ms (may be NULL) receives the best per-pass
+ * times [step-1 sums, drift].  Synchronising; overwrites only the partial-sum
+ * scratch. */
 ssm_status ssm_autotune(ssm_ctx *ctx, double *best_ms);
 
 /* The launch shape in use for which = 0 (step-1 sums) or 1 (drift):
@@ -269,7 +271,8 @@ ssm_status ssm_autotune(ssm_ctx *ctx, double *best_ms);
 ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
 
 /* Select a launch shape explicitly: in[3] = {form (0/1/2 as in ssm_get_plan),
- * threads per block, targets per thread}; the chunk count is planned as in ssm_autotune.
+ * threads per block, targets per thread}; the chunk count is planned (or fixed by
+ * ssm_opts.tile_chunks), not tuned.
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
 
