@@ -9,6 +9,8 @@ Sizes: small cases the oracle finishes in seconds over the full horizon (several
 tiles, ragged tails), plus the full workload sizes checked step by step on
 sampled particles, which the oracle computes one at a time.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -233,17 +235,21 @@ def test_coupled3d_fp32c_every_launch_shape(S, shape):
 
 
 def test_autotune_changes_shape_not_results(S):
-    N, h = 5000, 2.0 ** -8
+    """The tuned shape and chunk count sum the pair terms in another order; both runs
+    pass the same residual test (each root within 64 tol of the exact one under the
+    FP32 forms' stagnation rule), so K steps differ by at most K x 2 x 64 tol."""
+    N, h, K = 5000, 2.0 ** -8, 3
     runs = []
     for tune in (False, True):
         s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=12, precision=S.SSM_FP32C)
         if tune:
             best = s.autotune()
             assert np.all(best > 0)
-        s.run_steps(3)
+        s.run_steps(K)
         runs.append(s.get_state()[0])
         s.close()
-    assert np.max(np.abs(runs[0] - runs[1])) < 1e-8
+    tol = max(1e-10, 2.0 ** -27 * h * (1.0 + 64.0 / math.sqrt(N)))
+    assert np.max(np.abs(runs[0] - runs[1])) < K * 2 * 64 * tol
 
 
 def test_set_plan_rejects_unknown_shape(S):
