@@ -138,6 +138,32 @@ def test_lemma_4_1_inequalities(coef, d, Lv):
         assert np.dot(x - y, vhx - vhy) <= Lv / (1 - 2 * h * Lv) * np.sum((x - y) ** 2) + 1e-9
 
 
+@pytest.mark.parametrize("coef,d,h,Lv,Lvt,p", [(O.COEF_CUBIC1D_GAUSS, 1, 0.1, 1.0, 0.0, ()),
+                                               (O.COEF_COUPLED3D, 3, 2.0 ** -4, 1.0 / 16.0, 0.25, ()),
+                                               (O.COEF_COUPLED1D, 1, 2.0 ** -4, 1.0 / 16.0, 0.25, ()),
+                                               (O.COEF_GL2, 1, 0.05, 0.0, 0.25, (1.5, 0.5))])
+def test_lemma_4_2_moment_bound(coef, d, h, Lv, Lvt, p):
+    """Lemma 4.2 for step 1 against the frozen mu^X: with hat L_v = 1/2 + L_v and
+    C_T = |v(0, delta_0)|^2 / 2 (Remark on implied properties),
+        |Y_i|^2 <= |X_i|^2 (1 + 2 hat L_v h / (1 - 2 hat L_v h))
+                   + L_vt h / (1 - 2 hat L_v h) (1/N) sum_j |X_j|^2 + 2 C_T h / (1 - 2 hat L_v h).
+    Constants: v(0, delta_0) = 0 for all four sets (C_T = 0); L_v as in Lemma 4.1
+    (0 for -y^3); L_vt, the squared measure-Lipschitz constant: the coupled pair
+    term is 1/2 times the mean of a 1-Lipschitz function of z (1/4), GL2's term is
+    c mean(mu) (c^2); the cubic set does not depend on the measure."""
+    N = 200
+    P = O.problem(d=d, coef=coef, N=N, h=h, p=p)
+    x = inputs.gaussian_cloud(N, d, seed=17, scale=2.0)
+    y, it, bad = O.implicit_step(P, x)
+    assert bad == 0
+    hl = 0.5 + Lv
+    den = 1.0 - 2.0 * hl * h
+    assert den > 0
+    x2 = np.sum(x * x, axis=1)
+    rhs = x2 * (1.0 + 2.0 * hl * h / den) + Lvt * h / den * np.mean(x2)
+    assert np.all(np.sum(y * y, axis=1) <= rhs * (1 + 1e-12)), np.max(np.sum(y * y, axis=1) - rhs)
+
+
 # ---------------------------------------------------------------------------
 # Pairwise interaction: invariants
 # ---------------------------------------------------------------------------
