@@ -18,6 +18,13 @@ import numpy as np
 from . import SSM, SSM_FP32C, SSM_FP64, Batch, ssm_philox
 
 
+def weak_strong(x, ref):
+    """(epsilon_1, epsilon_2) of §3 between particle arrays x and ref, shape (N, d):
+    the norm of the mean difference and the root mean square of the differences."""
+    diff = np.asarray(x, dtype=np.float64) - np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(np.mean(diff, axis=0))), math.sqrt(float(np.mean(np.sum(diff * diff, axis=1))))
+
+
 def error_study(coef, d, T, ks, k_ref, N, seed, coef_params=(), x0_mean=0.0, x0_std=1.0, precision=SSM_FP64,
                 measure_y=0):
     """epsilon_1 and epsilon_2 at T for h = T 2^-k (k in ks) against h = T 2^-k_ref.
@@ -36,8 +43,9 @@ def error_study(coef, d, T, ks, k_ref, N, seed, coef_params=(), x0_mean=0.0, x0_
     for k in ks:
         x = run(k)
         hs.append(T * 2.0 ** -k)
-        weak.append(float(np.linalg.norm(np.mean(x - ref, axis=0))))
-        strong.append(math.sqrt(float(np.mean(np.sum((x - ref) ** 2, axis=1)))))
+        w, st = weak_strong(x, ref)
+        weak.append(w)
+        strong.append(st)
     lh = np.log2(hs)
     return dict(h=hs, weak=weak, strong=strong, weak_slope=float(np.polyfit(lh, np.log2(weak), 1)[0]),
                 strong_slope=float(np.polyfit(lh, np.log2(strong), 1)[0]))
@@ -86,10 +94,8 @@ def batch_study(descs, ref_log2=14, precision=SSM_FP32C, stream=None):
         refs = {k: b.get_state(i)[0] for k, i in ref_of.items()}
         per = []
         for e, dsc in enumerate(descs):
-            diff = b.get_state(e)[0] - refs[(dsc["d"], dsc["N"], dsc["T"], dsc["seed"])]
-            per.append(dict(e=e, d=dsc["d"], N=dsc["N"], h=dsc["h"],
-                            weak=float(np.linalg.norm(np.mean(diff, axis=0))),
-                            strong=math.sqrt(float(np.mean(np.sum(diff * diff, axis=1))))))
+            w, st = weak_strong(b.get_state(e)[0], refs[(dsc["d"], dsc["N"], dsc["T"], dsc["seed"])])
+            per.append(dict(e=e, d=dsc["d"], N=dsc["N"], h=dsc["h"], weak=w, strong=st))
     finally:
         b.close()
     by_h = {}
