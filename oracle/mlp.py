@@ -12,8 +12,6 @@ W4 [3][64], b4 [3].  Blob layout (32-bit words): header 8, feature mean 16, std
 16, label mean 4, std 4, b1 64, b2 64, b3 64, b4 4, then BF16 W1, W2, W3, W4
 (4 rows, the last zero).
 """
-import struct
-
 import numpy as np
 
 NI, NH, NO = 16, 64, 3

@@ -58,6 +58,5 @@ def test_float_to_double_is_exact(S):
 
 
 def test_conversion_check_validates_arguments(S):
-    import ctypes
     assert S.lib().ssm_convert_check(None, 3, None, None) == S.SSM_EINVAL
     assert S.lib().ssm_convert_check(None, 0, None, None) == S.SSM_OK
