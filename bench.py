@@ -28,21 +28,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PART, DIM, H, T_END, SEED = 1 << 18, 3, 2.0 ** -8, 1.0, 2
-FP32_LANES_PER_SM, N_SMS, MAX_SM_MHZ = 128, 152, 2070.0
-# Algorithmic FP32 flops per pair interaction (FFMA = 2, the special-function op
-# not counted): step-1 pair (x_j - y) / (1 + |x_j - y|^2) with its weight sum: 3
-# differences + 6 for 1 + |d|^2 + 6 for the weighted accumulation + 1 = 16; drift
-# pair (y_j - y) exp(-|d|^2 / 2): 3 differences + 5 for |d|^2 + 6 accumulation = 14.
-FLOPS_PAIR = {0: 16.0, 1: 14.0}          # 0: step-1 pair sums, 1: step-2 drift
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 flops per pair interaction (FFMA = 2, the special-function op not
+# counted), the counts of the method's direct formulas: step-1 residual pair
+# (x_j - y)/(1 + |x_j - y|^2): 3 differences, |d|^2 + 1 as 3 FFMA = 6, the weighted
+# accumulation 3 FFMA = 6, i.e. 15 (plus the weight sum 1: 16 with it); drift pair
+# (y_j - y) exp(-|d|^2/2): 3 differences, |d|^2 as 1 FMUL + 2 FFMA = 5, scaled exponent
+# argument 1, 3 FFMA = 6, i.e. 15.
+FLOPS_PAIR = {0: 15.0, 1: 15.0}          # 0: step-1 pair sums, 1: step-2 drift
+FLOPS_PAIR_WITH_WSUM = 16.0              # step-1 count including the weight sum
 # FP32 flops the centred-expansion kernels execute per pair (same sums, fewer
 # operations): step 1: 1 + 3 x 2 (q) + 3 x 2 + 1 = 14; drift: 3 x 2 + 3 x 2 + 1 = 13.
 FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
 FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
 # DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 4> at
-# N = 2^18, from ncu (profiles/launches_bench_coupled3d_N262144.md), for each source-chunk
-# count the autotuner can pick for that shape (the partial sums written grow with it);
-# valid only for the kernel sources they were measured on (their SHA-256 below),
-# otherwise the roofline's traffic is null.
+# N = 2^18, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for
+# each source-chunk count the autotuner can pick for that shape (the partial sums
+# written grow with it); valid only for the kernel sources they were measured on
+# (their SHA-256 below), otherwise the roofline's traffic is null.
 MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18),
                     "bytes_by_chunks": {13: 13454336 + 50698240, 19: 13403136 + 100761344,
                                         26: 13871104 + 159572736, 32: 15556608 + 210136320},
@@ -77,6 +80,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batched", type=int, default=1, help="also time the 64-ensemble batched form (1/0)")
     p.add_argument("--o-n", type=int, default=1, help="also time the O(N) kernels at N=2^26 against HBM (1/0)")
+    p.add_argument("--full-run", type=int, default=1, help="also time one ssm_run over the whole horizon (1/0)")
     p.add_argument("--profile-o-n", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: 4 steps of the O(N) coefficient set --profile-set at N = 2^LOG2N in "
                         "the form of --precision, and exit")
@@ -250,6 +254,8 @@ def run_reference(args, world, rank):
             "data": "synthetic: X_0 ~ N(0, I_3) from Philox4x32-10 seed 2",
             "config": {"workload": "coupled3d N=2^18 d=3 h=2^-8 T=1 seed=2 (FP64 oracle, sampled targets)",
                        "sample_targets_per_step": per, "l2": "n/a (CPU)"},
+            "sampled": "each step times %d of the N targets (each with its full O(N) work); value is targets/s, "
+                       "ms_per_step is N / value, an extrapolation to the whole step" % per,
             "cpu_baseline": dict(cb, value=v, sample="%d random targets per step, full O(N) work each" % per),
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -286,6 +292,31 @@ MOMENT_MODELS = {"gl1": (1, "SSM_COEF_GL1", (1.5, 0.5), 1.0, 0.0),
                  "poly": (1, "SSM_COEF_POLY", (-1.0,), 1.0, 0.0),
                  "cs": (2, "SSM_COEF_CS", (2.0, 4.0), 1.0, 2.0 ** 0.5)}
 ON_BYTES_PER_PARTICLE_STEP = 4 * 8 * ON_D   # implicit step: read X, write Y; step 2: read Y, write X (FP64)
+
+
+def measured_peaks():
+    """The generated MEASURED_PEAKS.json of this GPU type ({} if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def fp32_peak(torch, dev):
+    """FP32 CUDA-core peak in TFLOP/s: SMs (as the device reports them) x 128 FP32
+    lanes x 2 flops (FFMA) x the maximum SM clock (MEASURED_PEAKS.json's sm_max_mhz,
+    else the 2070 MHz nominal maximum); returns (TFLOP/s, basis, SMs, MHz)."""
+    sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    mhz = measured_peaks().get("sm_max_mhz")
+    src = "MEASURED_PEAKS.json sm_max_mhz"
+    if not mhz:
+        mhz, src = 2070.0, "nominal maximum SM clock"
+    mhz = float(mhz)
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    basis = ("FP32 CUDA-core: %d SMs (cudaDevAttrMultiProcessorCount via torch) x %d lanes x 2 flop x %.0f MHz (%s)"
+             % (sms, FP32_LANES_PER_SM, mhz, src))
+    return tf, basis, sms, mhz
 
 
 def hbm_peak_gbs():
@@ -451,8 +482,7 @@ def main():
     dom = 0 if share_newton >= t_drift else 1
     t_dom = t_newton if dom == 0 else t_drift
     flops = FLOPS_PAIR[dom] * N_PART * N_PART
-    sm_mhz = MAX_SM_MHZ
-    peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    peak, peak_basis, n_sms, sm_mhz = fp32_peak(torch, dev)
     achieved = flops / t_dom / 1e12
     dom_plan = plans["step1_pairs" if dom == 0 else "drift_pairs"]
     dom_form = dom_plan["form"]
@@ -464,9 +494,16 @@ def main():
                 "kernel": "%s<%s> (%s)" % (("k_pair", "k_pair2", "k_pair2x")[dom_form],
                                            "PK_NEWTON3" if dom == 0 else "PK_DRIFT3", FORM_NAMES[dom_form]),
                 "flops_per_pair": FLOPS_PAIR[dom],
+                "flops_basis": "algorithmic count of the direct pair formula: residual-only step-1 pair 15 flops, "
+                               "drift pair 15 (FFMA = 2, the special-function op not counted)",
+                "frac_with_weight_sum": (FLOPS_PAIR_WITH_WSUM * N_PART * N_PART / t_dom / 1e12 / peak
+                                         if dom == 0 else None),
                 "executed_tflops": executed, "executed_frac": executed / peak,
-                "peak_basis": "FP32 CUDA-core: 152 SMs x 128 lanes x 2 flop x 2070 MHz (recipe max clock)",
-                "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3}
+                "executed_flops_per_pair": (FLOPS_PAIR_EXPANDED if dom_form == 2 else FLOPS_PAIR)[dom],
+                "peak_basis": peak_basis, "sms": n_sms, "sm_max_mhz": sm_mhz,
+                "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3,
+                "other_pair_kernel_frac": FLOPS_PAIR[1 - dom] * N_PART * N_PART
+                / (t_drift if dom == 0 else t_newton) / 1e12 / peak}
 
     # end to end through the C ABI: pinned host state in, step, pinned host state out
     xh = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()
@@ -484,6 +521,38 @@ def main():
            "h2d_bytes_per_step": N_PART * DIM * 8, "d2h_bytes_per_step": N_PART * DIM * 8,
            "steps": e2e_steps}
     s.close()
+
+    # the whole horizon as a user runs it: one ssm_run of M = T/h = 256 steps from X_0,
+    # wall time from the first enqueue to the final stream sync (context creation,
+    # X_0 and tuning excluded; the shapes tuned above), one run
+    full_run = None
+    if args.full_run:
+        r = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+                  precision=prec)
+        if prec == S.SSM_FP32C_LEARNED:
+            S.load_ws(r)
+        for w in (0, 1):
+            pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
+            r.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"])
+        r.sync()
+        torch.cuda.synchronize()
+        fev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        t0 = time.perf_counter()
+        fev[0].record(stream)
+        r.run()
+        fev[1].record(stream)
+        r.sync()
+        wall = time.perf_counter() - t0
+        rst = r.stats()
+        M = rst["steps"]
+        full_run = {"value": N_PART * M / wall, "unit": "particle-steps/s", "steps": M, "wall_s": wall,
+                    "device_s": fev[0].elapsed_time(fev[1]) / 1e3, "runs": 1,
+                    "timing": "host wall clock from the first enqueue of ssm_run to the final stream sync; "
+                              "no L2 flush between steps",
+                    "newton_passes_per_step": rst["newton_passes"] / M,
+                    "newton_rows_per_step": rst["newton_rows"] / M, "max_passes": rst["max_passes"],
+                    "fallbacks": rst["fallbacks"], "floor_accepts": rst["floor_accepts"]}
+        r.close()
 
     # the same FP32C form without the learned start (same launch shapes, same timing)
     fp32c_plain = None
@@ -512,11 +581,24 @@ def main():
                        "newton_rows_per_step": (qs1["newton_rows"] - qs0["newton_rows"]) / args.steps}
         q.close()
 
-    # plain FP64 GPU SSM on the same workload (comparison of the metric)
+    # plain FP64 GPU SSM on the same workload (comparison of the metric): its own
+    # launch shapes (tuned on the same workload at N = 2^16, where a pass takes 1/16 of
+    # the time, and applied at 2^18), one untimed warm-up step, then the timed steps
     fp64 = None
     if args.fp64_steps > 0:
+        tq = S.SSM(d=DIM, N=1 << 16, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+                   precision=S.SSM_FP64)
+        tq.run_steps(1)
+        tq.autotune()
+        fplans = [tq.plan(0), tq.plan(1)]
+        tq.close()
         p = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
                   precision=S.SSM_FP64)
+        for w in (0, 1):
+            p.set_plan(w, fplans[w]["form"], fplans[w]["threads"], fplans[w]["targets_per_thread"])
+        p.run_steps(1)                      # warm-up step (untimed)
+        p.sync()
+        pst0 = p.stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream.synchronize()
         e0.record(stream)
@@ -526,8 +608,11 @@ def main():
         dt = e0.elapsed_time(e1) / 1e3
         pst = p.stats()
         fp64 = {"value": N_PART * args.fp64_steps / dt, "unit": "particle-steps/s", "steps": args.fp64_steps,
-                "ms_per_step": dt * 1e3 / args.fp64_steps,
-                "newton_passes_per_step": pst["newton_passes"] / max(1, pst["steps"])}
+                "warmup": 1, "ms_per_step": dt * 1e3 / args.fp64_steps,
+                "plans": {"step1_pairs": fplans[0], "drift_pairs": fplans[1]},
+                "timing": "CUDA events around %d step(s) after one warm-up step; shapes tuned at N=2^16"
+                          % args.fp64_steps,
+                "newton_passes_per_step": (pst["newton_passes"] - pst0["newton_passes"]) / args.fp64_steps}
         p.close()
 
     batched = bench_batched(torch, S, stream) if args.batched else None
@@ -571,6 +656,8 @@ def main():
             "batched_form": batched,
             "measure_y_form": measure_y,
             "o_n_kernels": o_n,
+            "full_run": full_run,
+            "floor_accepts_per_step": (st1["floor_accepts"] - st0["floor_accepts"]) / args.steps,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -136,6 +136,11 @@ typedef struct {
     int64_t fallbacks;       /* learned starts that missed the tolerance and restarted */
     int64_t max_passes;      /* largest pass count of one implicit step */
     int64_t hist[16];        /* particles that converged after k passes (last step), k < 16 */
+    int64_t floor_accepts;   /* FP32 forms: particles whose step-1 residual was still above
+                                newton_tol (at most 64 newton_tol) when its decrease from the
+                                previous pass fell below tenfold, the evaluation floor of FP32
+                                pair sums, and that were accepted there (0 in SSM_FP64).  With
+                                step 1 against mu^Y: those of each step's last pass. */
 } ssm_stats_t;
 
 typedef struct ssm_ctx ssm_ctx;

@@ -57,7 +57,7 @@ class ssm_opts(ctypes.Structure):
 
 class ssm_stats_t(ctypes.Structure):
     _fields_ = [("steps", _i64), ("newton_passes", _i64), ("newton_rows", _i64), ("drift_rows", _i64),
-                ("fallbacks", _i64), ("max_passes", _i64), ("hist", _i64 * 16)]
+                ("fallbacks", _i64), ("max_passes", _i64), ("hist", _i64 * 16), ("floor_accepts", _i64)]
 
 
 class SSMError(RuntimeError):
@@ -171,7 +171,7 @@ class Batch:
         s = ssm_stats_t()
         _check(lib().ssm_batch_stats(self.b, ctypes.byref(s)), "ssm_batch_stats")
         return {"ensemble_steps": s.steps, "newton_passes": s.newton_passes, "newton_rows": s.newton_rows,
-                "drift_rows": s.drift_rows, "batch_steps": s.max_passes}
+                "drift_rows": s.drift_rows, "batch_steps": s.max_passes, "floor_accepts": s.floor_accepts}
 
     def autotune(self):
         best = _dbl(0.0)
@@ -367,7 +367,7 @@ def ssm_stats(ctx):
     _check(lib().ssm_stats(ctx, ctypes.byref(s)), "ssm_stats")
     return {"steps": s.steps, "newton_passes": s.newton_passes, "newton_rows": s.newton_rows,
             "drift_rows": s.drift_rows, "fallbacks": s.fallbacks, "max_passes": s.max_passes,
-            "hist": [int(v) for v in s.hist]}
+            "hist": [int(v) for v in s.hist], "floor_accepts": s.floor_accepts}
 
 
 def ssm_destroy(ctx):

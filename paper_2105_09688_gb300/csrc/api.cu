@@ -34,6 +34,17 @@ cudaError_t launch_normals32(uint64_t seed, int d, int64_t N, uint32_t step, uin
 cudaError_t ws_forward_start(ssm_ctx *c);
 }  // namespace ssm
 
+namespace ssm {
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+}  // namespace ssm
+
 using namespace ssm;
 
 namespace {
@@ -80,9 +91,8 @@ int drift_kind(int coef) { return (coef == SSM_COEF_CUBIC1D_GAUSS || coef == SSM
 
 // Resident-block slots of the device for a pair kernel shape (0 = no device).
 int device_slots(int kind, bool fp32, int vec2, int threads, int rpt) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    const int sms = device_sms();
+    if (sms <= 0) return 0;
     const int nb = pair_blocks_per_sm(kind, fp32, vec2, threads, rpt);
     if (nb <= 0) { cudaGetLastError(); return 0; }
     return sms * nb;
@@ -158,7 +168,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
         part = (size_t)chunks_cap(N, 1);
     }
     L.part = take(sizeof(double) * part * Np);
-    L.mpart = take(sizeof(double) * RED_BLOCKS * 12);
+    L.mpart = take(sizeof(double) * RED_MAX_BLOCKS * 12);
     L.mom = take(sizeof(double) * 12);
     L.ymean = take(sizeof(double) * 4);
     const bool nt = is_coupled(coef);
@@ -175,7 +185,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.sconv = take(nt ? sizeof(double) * 3 * Np : 0);
     L.mom_prev = take(sizeof(double) * 12);
     L.rprev = take(nt ? sizeof(float) * Np : 0);
-    L.mif = take(nt ? sizeof(int) * 3 * (kmax + 2) : 0);
+    L.mif = take(nt ? sizeof(int) * MIF_WORDS(kmax) : 0);
     L.total = o;
     return L;
 }
@@ -388,6 +398,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->rprev = (float *)(b + L.rprev);
     c->mif = (int *)(b + L.mif);
     c->ws_loaded = 0;
+    c->sms = device_sms();
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0
     e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
@@ -514,6 +525,7 @@ ssm_status ssm_stats(ssm_ctx *c, ssm_stats_t *out) {
     out->drift_rows = cn[CNT_DRIFT_ROWS];
     out->fallbacks = cn[CNT_FALLBACKS];
     out->max_passes = cn[CNT_MAX_PASSES];
+    out->floor_accepts = cn[CNT_FLOOR];
     for (int k = 0; k < 16; ++k) out->hist[k] = hs[k];
     return harvest(c);
 }

@@ -209,7 +209,7 @@ __device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, in
     }
     Sw *= invN;
     const int r = newton_update_particle<D>(S, Sw, Y, X, E.h, E.tol, fp32, pass, kmax, -1, &E.rprev[i]);
-    if (r == UPD_CONTINUE || r == UPD_CONVERGED)
+    if (r == UPD_CONTINUE || r == UPD_CONVERGED || r == UPD_FLOOR)
 #pragma unroll
         for (int c = 0; c < D; ++c) E.y[c * E.Np + i] = Y[c];
     return r;
@@ -236,6 +236,7 @@ kb_update(BEns *ens, int n_ens, BGlobal *g, int kmax, int fp32, cudaGraphConditi
             const int r = E.d == 1 ? update_one<1>(E, pass, t, i, fp32 != 0, kmax)
                                    : update_one<3>(E, pass, t, i, fp32 != 0, kmax);
             if (r == UPD_CONTINUE) keep = true;
+            else if (r == UPD_FLOOR) atomicAdd((unsigned long long *)&g->counters[CNT_FLOOR], 1ull);
             else if (r == UPD_NOCONV) atomicOr(&g->err, ERR_NOCONV);
             else if (r == UPD_NONFINITE) atomicOr(&g->err, ERR_NONFINITE);
         }
@@ -505,10 +506,13 @@ cudaError_t build_graph(ssm_batch *b) {
 }
 
 int resident_grid(void *func, int threads) {
-    int dev = 0, sms = 0, nb = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 152;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0) != cudaSuccess || nb < 1) nb = 1;
+    int nb = 0;
+    int sms = device_sms();
+    if (sms <= 0) sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
     return sms * nb;
 }
 
@@ -601,7 +605,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         nseg_total += (D.N + SEGT - 1) / SEGT;
     }
     const size_t o_ens = take(sizeof(BEns) * n), o_g = take(sizeof(BGlobal)), o_seg = take(sizeof(long long) * (n + 1));
-    const size_t o_mseg = take(sizeof(double) * 12 * (size_t)nseg_total), o_mpart = take(sizeof(double) * RED_BLOCKS * 12);
+    const size_t o_mseg = take(sizeof(double) * 12 * (size_t)nseg_total), o_mpart = take(sizeof(double) * RED_MAX_BLOCKS * 12);
     const size_t o_tk = take(sizeof(unsigned)), o_err = take(sizeof(int));
     e = cudaMalloc((void **)&b->mem, o8);
     if (e != cudaSuccess) { if (b->own_stream) cudaStreamDestroy(b->st); delete b; return cuda_st(e); }
@@ -723,6 +727,7 @@ ssm_status ssm_batch_stats(ssm_batch *b, ssm_stats_t *out) {
     out->newton_rows = g.counters[CNT_NEWTON_ROWS];
     out->drift_rows = g.counters[CNT_DRIFT_ROWS];
     out->max_passes = g.bstep;   // batch steps taken
+    out->floor_accepts = g.counters[CNT_FLOOR];
     return harvest_batch(b);
 }
 

@@ -385,7 +385,7 @@ cudaError_t ws_forward_start(ssm_ctx *c) {
     cudaError_t e = set_smem_limits();
     if (e != cudaSuccess) return e;
     int64_t blocks = (c->N + 127) / 128;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
     k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
     return cudaGetLastError();
 }

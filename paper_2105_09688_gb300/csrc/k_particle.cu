@@ -329,9 +329,9 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
                 double *__restrict__ sconv, int restart_pass, long long *counters, float *__restrict__ rprev) {
     constexpr int NC = D + 1;
     __shared__ int bh[16];
-    __shared__ int nrestart;
+    __shared__ int nrestart, nfloor;
     if (threadIdx.x < 16) bh[threadIdx.x] = 0;
-    if (threadIdx.x == 0) nrestart = 0;
+    if (threadIdx.x == 0) { nrestart = 0; nfloor = 0; }
     __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n_in = *cnt_in;
@@ -358,9 +358,10 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
         Sw *= invN;
         const int r = newton_update_particle<D>(S, Sw, Y, X, h, tol, fp32_targets != 0, pass, kmax, restart_pass,
                                                 &rprev[i]);
-        if (r == UPD_CONVERGED) {
+        if (r == UPD_CONVERGED || r == UPD_FLOOR) {
             passes[i] = pass + 1;
             atomicAdd(&bh[pass + 1 < 15 ? pass + 1 : 15], 1);
+            if (r == UPD_FLOOR) atomicAdd(&nfloor, 1);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 y[c * Np + i] = Y[c];
@@ -391,6 +392,8 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
     if (threadIdx.x < 16 && bh[threadIdx.x]) atomicAdd((unsigned long long *)&hist[threadIdx.x], (unsigned long long)bh[threadIdx.x]);
     if (threadIdx.x == 0 && nrestart)
         atomicAdd((unsigned long long *)&counters[CNT_FALLBACKS], (unsigned long long)nrestart);
+    if (threadIdx.x == 0 && nfloor)
+        atomicAdd((unsigned long long *)&counters[CNT_FLOOR], (unsigned long long)nfloor);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,7 +427,7 @@ __global__ void k_mi_begin(const double *__restrict__ x, double *__restrict__ y,
     if (i == 0) {
         cnt[0] = (int)N;
         for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
-        for (int k = 0; k < 3 * (kmax + 1); ++k) flags[k] = 0;
+        for (int k = 0; k < MIF_WORDS(kmax); ++k) flags[k] = 0;
     }
 }
 
@@ -436,7 +439,7 @@ k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *
     constexpr int NC = D + 1;
     if (cnt[pass] == 0) return;   // converged at an earlier pass (grid-uniform)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool conv = true;
+    bool conv = true, floor_acc = false;
     float lb = 0.0f, mv = 0.0f;
     if (i < N) {
         double S[D], Sw = 0.0, Y[D], X[D];
@@ -472,6 +475,7 @@ k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *
         if (bad) atomicOr(err, ERR_NONFINITE);
         // FP32 sums: accepted at their evaluation floor as in the SSM's step 1
         conv = bad || rinf <= tol || (fp32 && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)rprev[i]);
+        floor_acc = conv && !bad && !(rinf <= tol);
         rprev[i] = (float)rinf;
         double u[D];
         local_root<D>(S, Sw, Y, X, h, u);
@@ -490,6 +494,8 @@ k_mi_update(const double *__restrict__ x, const double *__restrict__ y, double *
         mv = (float)dn * 1.0001f;
     }
     if (__any_sync(0xffffffffu, !conv) && (threadIdx.x & 31) == 0) atomicOr(&flags[pass], 1);
+    const unsigned fm = __ballot_sync(0xffffffffu, floor_acc);
+    if (fm && (threadIdx.x & 31) == 0) atomicAdd(&flags[MIF_FLOOR(kmax) + pass], __popc(fm));
     for (int o = 16; o > 0; o >>= 1) {
         lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, o));
         mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, o));
@@ -520,13 +526,15 @@ __global__ void k_mi_commit(double *__restrict__ y, const double *__restrict__ p
     }
 }
 
-// Work counters of one implicit step (one thread).
-__global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *counters) {
+// Work counters of one implicit step (one thread).  mi_flags (step 1 against mu^Y,
+// else null): the particles accepted at the FP32 floor in the step's last pass.
+__global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *counters, const int *mi_flags) {
     long long rows = 0, npass = 0;
     for (int k = 0; k < kmax; ++k) {
         rows += cnt[k];
         if (cnt[k] > 0) npass = k + 1;
     }
+    if (mi_flags && npass > 0) counters[CNT_FLOOR] += mi_flags[MIF_FLOOR(kmax) + npass - 1];
     counters[CNT_NEWTON_ROWS] += rows;
     counters[CNT_NEWTON_PASSES] += npass;
     if (npass > counters[CNT_MAX_PASSES]) counters[CNT_MAX_PASSES] = npass;
@@ -551,7 +559,7 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // EUL_OU (b = lambda mean(Y), sigma = eta, the same for every particle), EUL_GEN
 // (the other moment sets: b and sigma from Y and its means, moment_b / moment_sigma).
 enum : int { EUL_PAIR = 0, EUL_OU = 1, EUL_GEN = 2 };
-template <int D> constexpr int eul_min_blocks = D >= 2 ? EUL_MIN_BLOCKS : RED_BLOCKS / 152;
+template <int D> constexpr int eul_min_blocks = D >= 2 ? EUL_MIN_BLOCKS : RED_PER_SM;
 template <int D, bool F32, int FAM>
 __global__ void __launch_bounds__(EUL_THREADS, eul_min_blocks<D>)
 k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
@@ -722,9 +730,11 @@ __global__ void k_normals32(uint64_t seed, int64_t N, uint32_t step, uint32_t st
 // Host launchers (enqueue only).
 // ---------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
-static inline unsigned gs_blocks(int64_t n, int th) {   // grid-stride launch size
+static inline unsigned gs_blocks(int64_t n, int th) {   // grid-stride launch size: at most 8 blocks an SM
     const int64_t b = (n + th - 1) / th;
-    return (unsigned)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+    int sms = device_sms();
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 cudaError_t launch_init_x0(ssm_ctx *c) {
@@ -764,9 +774,9 @@ cudaError_t launch_mm_implicit(ssm_ctx *c) {
     const bool f32 = c->prec != SSM_FP64;
     const double p0 = c->opt.coef_params[0], p1 = c->opt.coef_params[1];
 #define SSM_MM(D) \
-    if (f32) k_mm_implicit<D, true><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
+    if (f32) k_mm_implicit<D, true><<<red_grid(c->sms, RED_PER_SM), EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
                                                                           p1, c->mom, c->mpart, c->ticket, c->ymean); \
-    else k_mm_implicit<D, false><<<RED_BLOCKS, EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
+    else k_mm_implicit<D, false><<<red_grid(c->sms, RED_PER_SM), EUL_THREADS, 0, c->st>>>(c->coef, c->x, c->y, c->N, c->Np, c->h, p0, \
                                                                        p1, c->mom, c->mpart, c->ticket, c->ymean);
     if (c->d == 1) { SSM_MM(1) }
     else if (c->d == 2) { SSM_MM(2) }
@@ -818,7 +828,7 @@ cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32) {
 }
 
 cudaError_t launch_step_stats(ssm_ctx *c) {
-    k_step_stats<<<1, 1, 0, c->st>>>(c->cnt, c->kmax, c->N, c->counters);
+    k_step_stats<<<1, 1, 0, c->st>>>(c->cnt, c->kmax, c->N, c->counters, c->opt.measure_y ? c->mif : nullptr);
     return cudaGetLastError();
 }
 
@@ -830,7 +840,7 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const bool f32 = c->prec != SSM_FP64;
     // families by dimension: d = 1 pair sets, OU, GL/POLY/GLSTAB; d = 2 OU, CS; d = 3 pair sets, OU
     const int fam = c->coef == SSM_COEF_OU ? EUL_OU : is_moment_set(c->coef) ? EUL_GEN : EUL_PAIR;
-#define SSM_EUL(D, F, G) k_euler<D, F, G><<<eul_min_blocks<D> * 152, EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
+#define SSM_EUL(D, F, G) k_euler<D, F, G><<<red_grid(c->sms, eul_min_blocks<D>), EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
         c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, \
         c->ticket, c->mom, c->err, c->counters)
 #define SSM_EUL_G(D, G) { if (f32) SSM_EUL(D, true, G); else SSM_EUL(D, false, G); }

@@ -11,7 +11,10 @@
 namespace ssm {
 
 // Outcome of one update of step 1 for a particle.
-enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 3, UPD_NONFINITE = 4 };
+// UPD_FLOOR: accepted at the FP32 evaluation floor of the residual (above tol, see
+// below); Y and S stay as for UPD_CONVERGED.
+enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 3, UPD_NONFINITE = 4,
+             UPD_FLOOR = 5 };
 
 // Step 1 of the coupled set, v(y, mu) = -y|y|^2 + 0.5 S(y), for one particle after
 // a pair pass: S[D] = (1/N) sum_j (X_j - fl(Y)) w_j and Sw = (1/N) sum_j w_j were
@@ -31,7 +34,8 @@ enum : int { UPD_CONVERGED = 0, UPD_CONTINUE = 1, UPD_RESTART = 2, UPD_NOCONV = 
 // N may lie above tol.  A pass normally cuts the residual by ~10^3; when it no
 // longer cuts it tenfold and the residual is within 64 tol, the iteration has
 // reached that floor and the particle is accepted (rprev holds the previous
-// pass's residual of this particle).
+// pass's residual of this particle); the outcome is then UPD_FLOOR, which the
+// kernels count (ssm_stats_t.floor_accepts).
 // Root u of the local model u = X + h(-u|u|^2 + 0.5(S - Sw (u - Y))) by Newton with
 // the Sherman-Morrison inverse of a I + 2h u u^T (a = 1 + h|u|^2 + 0.5 h Sw).
 template <int D>
@@ -83,7 +87,7 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
     }
     if (bad) return UPD_NONFINITE;
     if (rinf <= tol) return UPD_CONVERGED;
-    if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_CONVERGED;
+    if (fp32_targets && pass > 0 && rinf <= 64.0 * tol && rinf > 0.1 * (double)*rprev) return UPD_FLOOR;
     *rprev = (float)rinf;
     double u[D];
     local_root<D>(S, Sw, Y, X, h, u);

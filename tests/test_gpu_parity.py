@@ -290,6 +290,59 @@ def test_coupled3d_full_size_sampled_bench_configuration(S, learned):
     s.close()
 
 
+def test_coupled3d_learned_full_horizon_tolerances(S):
+    """The learned + FP32C form (the shipped network) over the whole horizon against
+    the FP64 oracle: N = 4096, h = 2^-8, T = 1 (256 steps), seed 2.  Bars: <= 1e-4
+    absolute per particle at T and <= 1e-5 on the empirical mean and variance.  The
+    learned start sees the late-time distribution of X here, not only X_0."""
+    N, h = 4096, 2.0 ** -8
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2, precision=S.SSM_FP32C_LEARNED)
+    S.load_ws(s)
+    s.run()
+    x, n = s.get_state()
+    m = s.moments()
+    st = s.stats()
+    s.close()
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=2)
+    xo = O.run(P, O.init_x0(P), 0, 256)
+    assert n == 256
+    assert np.max(np.abs(x - xo)) < 1e-4
+    mo = O.moments(P, xo)
+    assert np.max(np.abs(m[0] - mo[0])) < 1e-5
+    var_g, var_o = m[1] - m[0] ** 2, mo[1] - mo[0] ** 2
+    assert np.max(np.abs(var_g - var_o)) < 1e-5
+    # every implicit solve ended within the pass limit; the learned start saved passes
+    assert st["steps"] == 256 and st["max_passes"] < 12
+    assert st["newton_rows"] < 3 * N * 256
+    print("learned N=4096 to T: max|dx| %.3e, passes %d, rows/step %.1f, fallbacks %d, floor accepts %d"
+          % (np.max(np.abs(x - xo)), st["newton_passes"], st["newton_rows"] / 256, st["fallbacks"],
+             st["floor_accepts"]))
+
+
+@pytest.mark.parametrize("n_at", [128, 255])
+def test_coupled3d_learned_full_size_late_steps_sampled(S, n_at):
+    """N = 2^18 in the benchmark's launch configuration, learned form: the GPU runs
+    to step n_at, then one more step is checked on sampled particles against the
+    oracle from the GPU's own X_n (the late-time distribution the learned start
+    meets in the benchmark)."""
+    N, h = 1 << 18, 2.0 ** -8
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2, precision=S.SSM_FP32C_LEARNED)
+    S.load_ws(s)
+    s.set_plan(0, 2, 128, 4)
+    s.set_plan(1, 2, 128, 8)
+    s.run_steps(n_at)
+    st0 = s.stats()
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=2)
+    _sampled_step_check(S, s, P, 24, 2e-9, 6e-7, seed=n_at)
+    st1 = s.stats()
+    assert st1["steps"] == n_at + 1
+    print("learned N=2^18 step %d: passes %d, rows %d, fallbacks %d, floor accepts %d (over the first %d steps: %d)"
+          % (n_at, st1["newton_passes"] - st0["newton_passes"], st1["newton_rows"] - st0["newton_rows"],
+             st1["fallbacks"] - st0["fallbacks"], st1["floor_accepts"] - st0["floor_accepts"], n_at,
+             st0["floor_accepts"]))
+    s.close()
+
+
 def test_coupled3d_full_size_sampled_fp64(S):
     """N = 2^18 in FP64: one step, sampled, 1e-10 relative."""
     N, h = 1 << 18, 2.0 ** -8
