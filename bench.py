@@ -638,8 +638,10 @@ def main():
     my.close()
     o_n = bench_o_n(torch, S, stream) if args.o_n else None
 
-    kmax = 12
-    launches_per_step = 1 + 2 * kmax + 1 + 1 + 1 + 1 + (1 if form.startswith("learned") else 0)
+    # kernels of one step: k_newton_begin, the learned start (learned form), a pair-sum
+    # and an update launch per step-1 pass (a device-driven loop runs only the passes
+    # with work), k_step_stats, the drift pair sums, k_euler, k_advance
+    launches_per_step = 1 + (1 if form.startswith("learned") else 0) + 2 * newton_passes + 4
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
@@ -649,7 +651,7 @@ def main():
                        "l2": "flushed between timed steps (512 MB write, untimed)",
                        "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows,
                        "plans": plans},
-            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(round(launches_per_step * args.steps)),
             "fp32c_without_learned_start": fp32c_plain,
             "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
             "plain_fp64": fp64,

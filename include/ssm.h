@@ -408,7 +408,11 @@ ssm_status ssm_ws_params(const void *blob, size_t bytes, float *params);
  * coefficient set for the N particles y (device array, SoA: component c of
  * particle i at y[c*ld + i], ld >= N) into b (device array, same layout), on
  * `stream` (cudaStream_t, NULL = default stream).  Asynchronous.  The result is
- * the one ssm_get_stage(SSM_STAGE_B) reports after a step whose Y is y.
+ * the drift ssm_get_stage(SSM_STAGE_B) reports after a step whose Y is y, up to
+ * rounding: this entry point splits the sources into its own chunks, so the
+ * partial sums are grouped differently (SSM_FP64: to the rounding of the
+ * regrouped double sums; SSM_FP32C: within ~1e-9 absolute, from the FP32
+ * sub-tile sums).
  *
  * Its scratch is a fixed 8 MiB static device array inside the library (held by
  * every GPU that loads the library until the process exits), so d * ld must be
@@ -416,7 +420,8 @@ ssm_status ssm_ws_params(const void *blob, size_t bytes, float *params);
  * return SSM_ENOMEM and launch nothing.  The call allocates and frees nothing.
  * The first call on a device looks up the scratch array's device address on
  * that device (it must be current); make that first call before any stream
- * capture.  All calls share the scratch: calls that overlap on the GPU (other
+ * capture.  After cudaDeviceReset the device has a new context and the next
+ * call looks the address up again: make it before any capture as well.  All calls share the scratch: calls that overlap on the GPU (other
  * streams, unordered threads) race; calls on one stream are safe.  Nothing in
  * the scratch needs to start at zero.  SSM_EINVAL for null pointers, N < 1,
  * ld < N or an unsupported coef/precision. */

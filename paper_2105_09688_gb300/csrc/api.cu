@@ -18,7 +18,7 @@ cudaError_t launch_moments(ssm_ctx *c);
 cudaError_t launch_cardano(const double *x, double *y, int64_t n, double h, cudaStream_t st);
 cudaError_t launch_mm_implicit(ssm_ctx *c);
 cudaError_t launch_newton_begin(ssm_ctx *c);
-cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32);
+cudaError_t launch_newton_update(ssm_ctx *c, int pass, int fp32, cudaGraphConditionalHandle hpass);
 cudaError_t launch_step_stats(ssm_ctx *c);
 cudaError_t launch_mi_begin(ssm_ctx *c);
 cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32);
@@ -144,7 +144,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -186,6 +186,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.mom_prev = take(sizeof(double) * 12);
     L.rprev = take(nt ? sizeof(float) * Np : 0);
     L.mif = take(nt ? sizeof(int) * MIF_WORDS(kmax) : 0);
+    L.dpass = take(sizeof(int));
     L.total = o;
     return L;
 }
@@ -269,7 +270,48 @@ ssm_status harvest(ssm_ctx *c) {
     return (ssm_status)c->status;
 }
 
-// Enqueue one SSM step (no host synchronisation, safe to capture in a graph).
+// The passes of step 1 (coupled sets, measure mu^X) as one conditional WHILE node of
+// the graph being captured on c->st: its body -- the pair sums of the particles still
+// active and their update -- repeats until the update kernel finds none left (or
+// kmax passes were made), so only passes with work are launched.  The body is
+// captured on the side stream c->st_body into the node's body graph.
+cudaError_t enqueue_pass_loop(ssm_ctx *c, bool f32) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive || !c->st_body) return cudaErrorStreamCaptureUnsupported;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->st_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaStream_t main_st = c->st;
+    c->st = c->st_body;
+    cudaError_t eb = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, c->act0, c->cnt, c->N, c->Np, 1.0,
+                               c->part, c->st, c->dpass, (int64_t)(c->act1 - c->act0));
+    if (eb == cudaSuccess) eb = launch_newton_update(c, 0, f32 ? 1 : 0, h);
+    c->st = main_st;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c->st_body, &captured);
+    if (eb != cudaSuccess) return eb;
+    if (e != cudaSuccess) return e;
+    return cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Enqueue one SSM step (no host synchronisation).  Captured into the context's step
+// graph by ssm_run_steps (the coupled sets' pass loop is a graph node).
 cudaError_t enqueue_step(ssm_ctx *c) {
     cudaError_t e = cudaSuccess;
     const bool f32 = fp32_pairs(c);
@@ -299,17 +341,10 @@ cudaError_t enqueue_step(ssm_ctx *c) {
             if ((e = launch_mi_pass(c, k, f32 ? 1 : 0)) != cudaSuccess) return e;
         }
     } else {
-    if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
+        if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
         if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
             if ((e = ws_forward_start(c)) != cudaSuccess) return e;
-        int *a_in = c->act0, *a_out = c->act1;
-        for (int k = 0; k < c->kmax; ++k) {
-            if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, a_in, c->cnt + k, c->N, c->Np,
-                               1.0, c->part, c->st)) != cudaSuccess)
-                return e;
-            if ((e = launch_newton_update(c, k, a_in, a_out, f32 ? 1 : 0)) != cudaSuccess) return e;
-            int *t = a_in; a_in = a_out; a_out = t;
-        }
+        if ((e = enqueue_pass_loop(c, f32)) != cudaSuccess) return e;
     }
     if ((e = launch_step_stats(c)) != cudaSuccess) return e;
     if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale,
@@ -366,8 +401,18 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
         if (e != cudaSuccess) { delete c; return cuda_status(e); }
         c->own_stream = true;
     }
+    c->st_body = nullptr;
+    if (is_coupled(coef) && !o.measure_y) {
+        e = cudaStreamCreateWithFlags(&c->st_body, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            if (c->own_stream) cudaStreamDestroy(c->st);
+            delete c;
+            return cuda_status(e);
+        }
+    }
     if (o.workspace) {
         if (o.workspace_bytes < L.total || ((uintptr_t)o.workspace & 255u)) {
+            if (c->st_body) cudaStreamDestroy(c->st_body);
             if (c->own_stream) cudaStreamDestroy(c->st);
             delete c;
             return o.workspace_bytes < L.total ? SSM_ENOMEM : SSM_EINVAL;
@@ -377,6 +422,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     } else {
         e = cudaMalloc((void **)&c->ws, L.total);
         if (e != cudaSuccess) {
+            if (c->st_body) cudaStreamDestroy(c->st_body);
             if (c->own_stream) cudaStreamDestroy(c->st);
             delete c;
             return cuda_status(e);
@@ -399,6 +445,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->mif = (int *)(b + L.mif);
     c->ws_loaded = 0;
     c->sms = device_sms();
+    c->dpass = (int *)(b + L.dpass);
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0
     e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
@@ -413,12 +460,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
 
 ssm_status ssm_step(ssm_ctx *c) {
     if (!c) return SSM_EINVAL;
-    if (c->status != SSM_OK) return (ssm_status)c->status;
-    if (c->n >= c->M) return SSM_ESTATE;
-    cudaError_t e = enqueue_step(c);
-    if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
-    c->n += 1;
-    return SSM_OK;
+    return ssm_run_steps(c, 1);
 }
 
 ssm_status ssm_run_steps(ssm_ctx *c, int64_t k) {
@@ -535,6 +577,7 @@ void ssm_destroy(ssm_ctx *c) {
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->graph_ready) cudaGraphExecDestroy(c->gexec);
     if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->st_body) cudaStreamDestroy(c->st_body);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }

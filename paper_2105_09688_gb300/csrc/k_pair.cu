@@ -11,11 +11,15 @@
 namespace ssm {
 
 // act/cnt: optional compacted target list (targets t < *cnt are particles act[t]).
+// dpass (optional): the pass index of step 1 in device memory, for launches inside a
+// device-driven pass loop; then the list is act + (pass & 1) act_stride (the two
+// ping-pong lists) and its length cnt[pass].
 template <int KIND, typename T, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS)
 k_pair(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
        const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-       double *__restrict__ part) {
+       double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
+    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
     const int64_t ntgt = act ? (int64_t)(*cnt) : N;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;   // block-uniform
@@ -29,7 +33,8 @@ template <int KIND, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS)
 k_pair2(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
         const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-        double *__restrict__ part) {
+        double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
+    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
     const int64_t ntgt = act ? (int64_t)(*cnt) : N;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;
@@ -44,7 +49,8 @@ template <int KIND, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS, packed_min_blocks(THREADS, R))
 k_pair2x(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
          const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-         double *__restrict__ part) {
+         double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
+    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
     const int64_t ntgt = act ? (int64_t)(*cnt) : N;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;
@@ -56,21 +62,26 @@ k_pair2x(const double *__restrict__ src, const double *__restrict__ tgt, const i
 
 template <int KIND, typename T, int THREADS, int R>
 static cudaError_t launch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
-                          int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+                          int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
+                          int64_t act_stride) {
     const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)p.chunks);
-    k_pair<KIND, T, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+    k_pair<KIND, T, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part, dpass,
+                                                          act_stride);
     return cudaGetLastError();
 }
 template <int KIND, int THREADS, int R>
 static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
-                           int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+                           int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
+                           int64_t act_stride) {
     const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)p.chunks);
     if (p.vec2 == 2)
-        k_pair2x<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+        k_pair2x<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part,
+                                                             dpass, act_stride);
     else
-        k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part);
+        k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part,
+                                                            dpass, act_stride);
     return cudaGetLastError();
 }
 
@@ -81,33 +92,40 @@ static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, 
 
 template <int KIND, typename T>
 static cudaError_t dispatch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
-                            int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+                            int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
+                            int64_t act_stride) {
 #define SSM_CASE(TH, RR) \
-    if (p.threads == TH && p.rpt == RR) return launch<KIND, T, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+    if (p.threads == TH && p.rpt == RR) \
+        return launch<KIND, T, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
     SSM_PAIR_SHAPES(SSM_CASE)
 #undef SSM_CASE
     return cudaErrorInvalidValue;
 }
 template <int KIND>
 static cudaError_t dispatch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
-                             int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+                             int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
+                             int64_t act_stride) {
 #define SSM_CASE(TH, RR) \
-    if (p.threads == TH && p.rpt == RR) return launch2<KIND, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+    if (p.threads == TH && p.rpt == RR) \
+        return launch2<KIND, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
     SSM_PAIR2_SHAPES(SSM_CASE)
 #undef SSM_CASE
     return cudaErrorInvalidValue;
 }
 
 cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
-                      const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st) {
+                      const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st,
+                      const int *dpass, int64_t act_stride) {
     if (fp32 && p.vec2) {
-        if (kind == PK_NEWTON3) return dispatch2<PK_NEWTON3>(p, src, tgt, act, cnt, N, Np, scale, part, st);
-        if (kind == PK_DRIFT3) return dispatch2<PK_DRIFT3>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+        if (kind == PK_NEWTON3)
+            return dispatch2<PK_NEWTON3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+        if (kind == PK_DRIFT3)
+            return dispatch2<PK_DRIFT3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
         return cudaErrorInvalidValue;
     }
 #define SSM_KIND(K) \
-    case K: return fp32 ? dispatch<K, float>(p, src, tgt, act, cnt, N, Np, scale, part, st) \
-                        : dispatch<K, double>(p, src, tgt, act, cnt, N, Np, scale, part, st);
+    case K: return fp32 ? dispatch<K, float>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride) \
+                        : dispatch<K, double>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
     switch (kind) {
         SSM_KIND(PK_DRIFT1)
         SSM_KIND(PK_DRIFT3)

@@ -304,7 +304,8 @@ k_mm_implicit(int coef, const double *__restrict__ x, double *__restrict__ y, in
 template <int D>
 __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
                                int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
-                               const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np) {
+                               const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np,
+                               int *__restrict__ dpass) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
 #pragma unroll
@@ -317,17 +318,30 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
         for (int k = 1; k <= kmax; ++k) cnt[k] = 0;
         for (int k = 0; k < 16; ++k) hist[k] = 0;
         for (int k = 0; k < 4 * D; ++k) mom_prev[k] = mom[k];
+        *dpass = 0;
     }
 }
 
+// One pass's update of every active particle.  The pass index and the active lists:
+// pass = *dpass inside the device-driven pass loop of the step graph (dpass non-null;
+// the last block then advances *dpass and sets the loop's condition hpass: another
+// pass while particles remain and pass + 1 < kmax), else pass_arg; the particles of
+// the pass are act[pass & 1][0 .. cnt[pass]) and the survivors go to the other list
+// and cnt[pass + 1].
 template <int D>
 __global__ void __launch_bounds__(256)
-k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int *__restrict__ act_in,
-                const int *__restrict__ cnt_in, int *__restrict__ act_out, int *__restrict__ cnt_out,
-                const double *__restrict__ part, int chunks, int64_t N, int64_t Np, double h, double tol,
-                int fp32_targets, int pass, int kmax, int *__restrict__ passes, long long *hist, int *err,
-                double *__restrict__ sconv, int restart_pass, long long *counters, float *__restrict__ rprev) {
+k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act0,
+                int *__restrict__ act1, int *__restrict__ cnt, const double *__restrict__ part, int chunks,
+                int64_t N, int64_t Np, double h, double tol, int fp32_targets, int pass_arg, int kmax,
+                int *__restrict__ passes, long long *hist, int *err, double *__restrict__ sconv, int restart_pass,
+                long long *counters, float *__restrict__ rprev, int *__restrict__ dpass, unsigned *ticket,
+                cudaGraphConditionalHandle hpass) {
     constexpr int NC = D + 1;
+    const int pass = dpass ? *dpass : pass_arg;
+    const int *__restrict__ act_in = (pass & 1) ? act1 : act0;
+    int *__restrict__ act_out = (pass & 1) ? act0 : act1;
+    const int *cnt_in = cnt + pass;
+    int *cnt_out = cnt + pass + 1;
     __shared__ int bh[16];
     __shared__ int nrestart, nfloor;
     if (threadIdx.x < 16) bh[threadIdx.x] = 0;
@@ -394,6 +408,11 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, const int 
         atomicAdd((unsigned long long *)&counters[CNT_FALLBACKS], (unsigned long long)nrestart);
     if (threadIdx.x == 0 && nfloor)
         atomicAdd((unsigned long long *)&counters[CNT_FLOOR], (unsigned long long)nfloor);
+    if (dpass && last_block(ticket) && threadIdx.x == 0) {
+        const int next = __ldcg(cnt_out);   // every block's appends are complete and visible
+        *dpass = pass + 1;
+        cudaGraphSetConditional(hpass, (next > 0 && pass + 1 < kmax) ? 1u : 0u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -788,18 +807,21 @@ cudaError_t launch_mm_implicit(ssm_ctx *c) {
 cudaError_t launch_newton_begin(ssm_ctx *c) {
     if (c->d == 1)
         k_newton_begin<1><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
-                                                              c->mom, c->mom_prev, c->N, c->Np);
+                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass);
     else
         k_newton_begin<3><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
-                                                              c->mom, c->mom_prev, c->N, c->Np);
+                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass);
     return cudaGetLastError();
 }
 
-cudaError_t launch_newton_update(ssm_ctx *c, int pass, const int *act_in, int *act_out, int fp32) {
+// Update of pass `pass` (hpass == 0), or of the pass *c->dpass inside the step
+// graph's device-driven loop whose condition is hpass.
+cudaError_t launch_newton_update(ssm_ctx *c, int pass, int fp32, cudaGraphConditionalHandle hpass) {
     const int rp = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1;
-#define SSM_UPD(D) k_newton_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, act_in, c->cnt + pass, act_out, \
-        c->cnt + pass + 1, c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->passes, \
-        c->hist, c->err, c->sconv, rp, c->counters, c->rprev)
+    int *dp = hpass ? c->dpass : nullptr;
+#define SSM_UPD(D) k_newton_update<D><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->act1, c->cnt, \
+        c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->passes, c->hist, c->err, \
+        c->sconv, rp, c->counters, c->rprev, dp, c->ticket, hpass)
     if (c->d == 1) SSM_UPD(1);
     else SSM_UPD(3);
 #undef SSM_UPD

@@ -8,7 +8,9 @@
 // embedders that budget every byte of device memory up front.  For them this
 // entry point computes the same drift as ssm_get_stage(SSM_STAGE_B) from caller
 // arrays, with its scratch (the per-chunk partial sums of the pair kernel) in
-// the fixed, file-scope device array below instead of a context workspace.
+// the fixed, file-scope device array below instead of a context workspace.  It
+// groups the pair sums in its own chunks, so it agrees with the context's drift
+// to rounding, not bit for bit.
 //
 // Properties callers rely on:
 //  - The scratch array is static device memory of SCRATCH_DOUBLES doubles
@@ -18,7 +20,11 @@
 //    sizes return SSM_ENOMEM (scratch too small) without launching anything.
 //  - The first call on a device looks up the device address of the scratch array
 //    (cudaGetSymbolAddress, with that device current); make that first call
-//    before any stream capture on that device.
+//    before any stream capture on that device.  The address is kept per device
+//    together with the identity of the CUDA context it belongs to: after
+//    cudaDeviceReset (a new primary context, the module loaded again) the next
+//    call on that device looks it up again, so that call too must come before any
+//    stream capture.
 //  - No call allocates or frees device or host memory.
 //  - Every call uses the same scratch array: calls whose work overlaps on the GPU
 //    (different streams, or different host threads without ordering) race on it.
@@ -43,19 +49,51 @@ static __device__ __align__(256) double g_scratch[SCRATCH_DOUBLES];
 
 std::mutex g_mu;
 double *g_scratch_ptr[MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {};   // context identity the address belongs to
 
-// Device address of g_scratch on the current device (looked up once per device).
+// The driver's context-identity query, fetched through the runtime (no link-time
+// dependency on the driver library): cuCtxGetCurrent and cuCtxGetId, CUDA 12.0.
+typedef int (*ctx_current_fn)(void **);
+typedef int (*ctx_id_fn)(void *, unsigned long long *);
+ctx_current_fn g_ctx_current = nullptr;
+ctx_id_fn g_ctx_id = nullptr;
+std::once_flag g_ctx_once;
+
+// Identity of the current CUDA context (0 if the driver cannot tell).
+unsigned long long current_context_id() {
+    std::call_once(g_ctx_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (ctx_current_fn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (ctx_id_fn)f;
+        cudaGetLastError();
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!g_ctx_current || !g_ctx_id || g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_scratch on the current device: looked up once per device
+// and context (again after a device reset gave the device a new context).
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = (double *)p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -115,7 +153,8 @@ extern "C" ssm_status ssm_drift_noalloc(int coef, int precision, int64_t N, cons
     const double bscale = cb / ((double)N * scale);
     e = pair_sums(kind, f32, p, y, y, nullptr, nullptr, N, ld, scale, scratch, st);
     if (e != cudaSuccess) return SSM_ECUDA;
-    const int64_t blocks = (N + 255) / 256 < 1216 ? (N + 255) / 256 : 1216;
+    const int64_t cap = (int64_t)sms * 8;   // grid-stride: at most 8 blocks an SM
+    const int64_t blocks = (N + 255) / 256 < cap ? (N + 255) / 256 : cap;
     k_combine_drift<<<(unsigned)blocks, 256, 0, st>>>(scratch, p.chunks, d, N, ld, bscale, b);
     return cudaGetLastError() == cudaSuccess ? SSM_OK : SSM_ECUDA;
 }

@@ -60,6 +60,32 @@ def test_noalloc_drift_matches_the_context_drift_twice(env, case):
             assert np.max(np.abs(b - b_ref)) < 1e-9, call
 
 
+@pytest.mark.parametrize("case", ["cubic1d_fp64", "coupled3d_fp32c"])
+def test_noalloc_drift_matches_the_oracle(env, case):
+    """The same entry point against the FP64 oracle's drift b(Y_i, mu^Y) of every
+    particle, on a seeded cloud: FP64 1e-10 relative; FP32C 5e-7 absolute (the
+    bound the pair-kernel shapes meet against the oracle)."""
+    import oracle as O
+    from tests import inputs
+    torch, S = env
+    coef, ocoef, d, prec, N = {
+        "cubic1d_fp64": (S.SSM_COEF_CUBIC1D_GAUSS, O.COEF_CUBIC1D_GAUSS, 1, S.SSM_FP64, 1500),
+        "coupled3d_fp32c": (S.SSM_COEF_COUPLED3D, O.COEF_COUPLED3D, 3, S.SSM_FP32C, 2500),
+    }[case]
+    y = inputs.heavy_cloud(N, d, seed=81)
+    ydev = torch.from_numpy(np.ascontiguousarray(y.T)).cuda()
+    bdev = torch.empty((d, N), dtype=torch.float64, device="cuda")
+    S.ssm_drift_noalloc(coef, prec, N, ydev.data_ptr(), N, bdev.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    b = bdev.cpu().numpy().T
+    P = O.problem(d=d, coef=ocoef, N=N, h=2.0 ** -8)
+    bo = np.stack([O.drift_one(P, y, i) for i in range(N)])
+    if prec == S.SSM_FP64:
+        assert np.max(np.abs(b - bo) / np.maximum(1.0, np.abs(bo))) < 1e-10
+    else:
+        assert np.max(np.abs(b - bo)) < 5e-7
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     torch, S = env
     buf = torch.zeros(8, dtype=torch.float64, device="cuda")
