@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--batched", type=int, default=1, help="also time the 64-ensemble batched form (1/0)")
     p.add_argument("--o-n", type=int, default=1, help="also time the O(N) kernels at N=2^26 against HBM (1/0)")
     p.add_argument("--full-run", type=int, default=1, help="also time one ssm_run over the whole horizon (1/0)")
+    p.add_argument("--fixed-passes", type=int, default=0, choices=[0, 1],
+                   help="step graphs with a fixed sequence of step-1 pass launches instead of the device-driven "
+                        "loop (for profilers that do not follow conditional graph nodes)")
     p.add_argument("--profile-o-n", type=int, default=0, metavar="LOG2N",
                    help="profiling driver: 4 steps of the O(N) coefficient set --profile-set at N = 2^LOG2N in "
                         "the form of --precision, and exit")
@@ -113,6 +116,7 @@ def profile_kernels(args):
     import paper_2105_09688_gb300 as S
     prec = S.SSM_FP32C if args.precision == "fp32c" else S.SSM_FP64
     s = S.SSM(d=DIM, N=1 << args.profile_kernels, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=SEED, precision=prec,
+              fixed_pass_launches=args.fixed_passes,
               measure_y=args.measure_y, tile_chunks=args.chunks)
     if args.packed:
         s.set_plan(0, args.packed, 128, args.rpt)
@@ -440,7 +444,8 @@ def main():
     form = "fp32c"
     if os.path.exists(os.path.join(ROOT, "paper_2105_09688_gb300", "ws_weights.bin")) and hasattr(S, "load_ws"):
         prec, form = S.SSM_FP32C_LEARNED, "learned+fp32c"
-    s = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream, precision=prec)
+    s = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream, precision=prec,
+              fixed_pass_launches=args.fixed_passes)
     if prec == S.SSM_FP32C_LEARNED:
         S.load_ws(s)
     s.run_steps(1)
@@ -641,7 +646,8 @@ def main():
     # kernels of one step: k_newton_begin, the learned start (learned form), a pair-sum
     # and an update launch per step-1 pass (a device-driven loop runs only the passes
     # with work), k_step_stats, the drift pair sums, k_euler, k_advance
-    launches_per_step = 1 + (1 if form.startswith("learned") else 0) + 2 * newton_passes + 4
+    launches_per_step = (1 + (1 if form.startswith("learned") else 0) + 4
+                         + 2 * (S.ssm_opts_default().newton_kmax if args.fixed_passes else newton_passes))
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",

@@ -47,7 +47,10 @@ typedef enum {
     SSM_ENOCONV = 4,     /* an implicit solve missed its tolerance within newton_kmax passes */
     SSM_ENONFINITE = 5,  /* a particle state became NaN or infinite */
     SSM_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
-    SSM_ESTATE = 7       /* call not valid in the context's state (e.g. past t = T) */
+    SSM_ESTATE = 7,      /* call not valid in the context's state (e.g. past t = T) */
+    SSM_EBOUNDS = 8      /* debug build only (ssm_build_flags): a kernel index fell outside the
+                            array it addresses; the access was skipped (results of that call
+                            are not valid) */
 } ssm_status;
 
 /* Coefficient sets (v, b, sigma) built into the library.
@@ -126,6 +129,18 @@ typedef struct {
                                §1 contrasts with the SSM, solved by block-Jacobi passes (each
                                an O(N^2) pair pass at the common iterate) to newton_tol.
                                Not with SSM_FP32C_LEARNED. */
+    int fixed_pass_launches; /* 0 (default): the passes of step 1 (coupled sets against mu^X)
+                               run as a device-driven loop, a conditional node of the step's
+                               CUDA graph that launches only passes with work.  1: the step
+                               graph holds newton_kmax pass launches, those past the last
+                               working pass exit at once -- for profilers that do not follow
+                               conditional graph nodes.  Same arithmetic, same results. */
+    int inject;             /* test hook of the debug build (ssm_build_flags() has
+                               SSM_BUILD_CHECK_BOUNDS): 1 = every step-1 start plants particle
+                               index N in entry 0 of the active list (coupled sets against mu^X,
+                               N not a multiple of 128, so the index lies inside the padded
+                               arrays) for the bounds checks to report as SSM_EBOUNDS.  Must be 0
+                               otherwise (SSM_EINVAL). */
 } ssm_opts;
 
 typedef struct {
@@ -202,6 +217,16 @@ void ssm_destroy(ssm_ctx *ctx);
 
 /* Human-readable name of a status code. */
 const char *ssm_status_str(int status);
+
+/* Build variant of the loaded library: a bit set of SSM_BUILD_* (0 = release).
+ * SSM_BUILD_CHECK_BOUNDS: compiled with SSM_CHECK_BOUNDS, the debug build whose
+ * kernels check the indices they take from data (active lists, counts, ensemble
+ * lookups) against the arrays they address, skip an access that falls outside and
+ * report it as SSM_EBOUNDS at the next synchronising call, without trapping (a
+ * stand-in for a memory checker).  Its words are per process, so a hit is
+ * reported by the next synchronising call of any context or batch. */
+enum { SSM_BUILD_CHECK_BOUNDS = 1 };
+int ssm_build_flags(void);
 
 /* ---- component entry points (the same device code as the step, for checks) ---- */
 

@@ -28,13 +28,17 @@ __all__ = [
     "ssm_ws_num_params",
 ]
 
-SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE = range(8)
+SSM_OK, SSM_EINVAL, SSM_ENOMEM, SSM_ECUDA, SSM_ENOCONV, SSM_ENONFINITE, SSM_ETIMEOUT, SSM_ESTATE, SSM_EBOUNDS = range(9)
+SSM_BUILD_CHECK_BOUNDS = 1
 SSM_COEF_CUBIC1D_GAUSS, SSM_COEF_COUPLED3D, SSM_COEF_OU, SSM_COEF_COUPLED1D = 0, 1, 2, 3
 SSM_COEF_GL1, SSM_COEF_GL2, SSM_COEF_POLY, SSM_COEF_CS, SSM_COEF_GLSTAB = 4, 5, 6, 7, 8
 SSM_FP64, SSM_FP32C, SSM_FP32C_LEARNED = 0, 1, 2
 SSM_STAGE_Y, SSM_STAGE_B = 0, 1
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libssm.so")
+# SSM_LIB_VARIANT=check selects the debug build libssm_check.so (bounds-checked
+# kernels, see ssm_build_flags); the default is the release library.
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                        "libssm_check.so" if os.environ.get("SSM_LIB_VARIANT") == "check" else "libssm.so")
 # Learned-start network trained by train_ws.py (rows from plain-SSM runs, seeds 100..163).
 WS_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "ws_weights.bin")
 
@@ -52,7 +56,7 @@ class ssm_opts(ctypes.Structure):
     _fields_ = [("precision", _i32), ("newton_tol", _dbl), ("newton_kmax", _i32), ("fine_log2", _i32),
                 ("x0_mean", _dbl), ("x0_std", _dbl), ("coef_params", _dbl * 4), ("stream", _vp),
                 ("workspace", _vp), ("workspace_bytes", _sz), ("tile_chunks", _i32), ("ws_passes", _i32),
-                ("measure_y", _i32)]
+                ("measure_y", _i32), ("fixed_pass_launches", _i32), ("inject", _i32)]
 
 
 class ssm_stats_t(ctypes.Structure):
@@ -85,6 +89,7 @@ _SIGS = {
     "ssm_stats": (_i32, [_vp, ctypes.POINTER(ssm_stats_t)]),
     "ssm_destroy": (None, [_vp]),
     "ssm_status_str": (ctypes.c_char_p, [_i32]),
+    "ssm_build_flags": (_i32, []),
     "ssm_philox": (_i32, [_u64, _U32P, _i64, _U32P]),
     "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
     "ssm_normals_fp32": (_i32, [_u64, _i32, _i64, _i64, _i32, ctypes.POINTER(ctypes.c_float)]),
@@ -275,7 +280,7 @@ def lib():
     global _LIB
     if _LIB is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libssm.so is not built (%s); run paper_2105_09688_gb300.build.build()" % LIB_PATH)
+            raise RuntimeError("%s is not built; run paper_2105_09688_gb300.build.build()" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)

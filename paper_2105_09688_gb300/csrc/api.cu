@@ -43,6 +43,14 @@ int device_sms() {
     }
     return sms;
 }
+int bounds_hits_all() {
+#ifdef SSM_CHECK_BOUNDS
+    const int a = bounds_hits_pair(), b = bounds_hits_particle(), c = bounds_hits_batch();
+    return a | b | c;
+#else
+    return 0;
+#endif
+}
 }  // namespace ssm
 
 using namespace ssm;
@@ -247,7 +255,14 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
         const double r = h / hf;
         if (r < 1.0 || fabs(nearbyint(r) - r) > 1e-9) return SSM_EINVAL;
     }
-    if (o.tile_chunks < 0) return SSM_EINVAL;
+    if (o.tile_chunks < 0 || o.fixed_pass_launches < 0 || o.fixed_pass_launches > 1) return SSM_EINVAL;
+    // ssm_opts.inject: only in the debug build, only the planted list entry of step 1
+    // (coupled sets against mu^X) at an N whose padded arrays extend past particle N
+#ifdef SSM_CHECK_BOUNDS
+    if (o.inject != 0 && (o.inject != 1 || !is_coupled(coef) || o.measure_y || N % 128 == 0)) return SSM_EINVAL;
+#else
+    if (o.inject != 0) return SSM_EINVAL;
+#endif
     return SSM_OK;
 }
 
@@ -267,6 +282,7 @@ ssm_status harvest(ssm_ctx *c) {
     if (e & ERR_NONFINITE) c->status = SSM_ENONFINITE;
     else if (e & ERR_NOCONV) c->status = SSM_ENOCONV;
     else if (e & ERR_TIMEOUT) c->status = SSM_ETIMEOUT;
+    else if (bounds_hits_all()) c->status = SSM_EBOUNDS;
     return (ssm_status)c->status;
 }
 
@@ -344,7 +360,16 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
         if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
             if ((e = ws_forward_start(c)) != cudaSuccess) return e;
-        if ((e = enqueue_pass_loop(c, f32)) != cudaSuccess) return e;
+        if (c->opt.fixed_pass_launches) {
+            for (int k = 0; k < c->kmax; ++k) {
+                if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, (k & 1) ? c->act1 : c->act0,
+                                   c->cnt + k, c->N, c->Np, 1.0, c->part, c->st)) != cudaSuccess)
+                    return e;
+                if ((e = launch_newton_update(c, k, f32 ? 1 : 0, 0)) != cudaSuccess) return e;
+            }
+        } else if ((e = enqueue_pass_loop(c, f32)) != cudaSuccess) {
+            return e;
+        }
     }
     if ((e = launch_step_stats(c)) != cudaSuccess) return e;
     if ((e = pair_sums(drift_kind(c->coef), f32, c->plan_drift, c->y, c->y, nullptr, nullptr, c->N, c->Np, scale,
@@ -402,7 +427,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
         c->own_stream = true;
     }
     c->st_body = nullptr;
-    if (is_coupled(coef) && !o.measure_y) {
+    if (is_coupled(coef) && !o.measure_y && !o.fixed_pass_launches) {
         e = cudaStreamCreateWithFlags(&c->st_body, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             if (c->own_stream) cudaStreamDestroy(c->st);
@@ -582,6 +607,14 @@ void ssm_destroy(ssm_ctx *c) {
     delete c;
 }
 
+int ssm_build_flags(void) {
+#ifdef SSM_CHECK_BOUNDS
+    return SSM_BUILD_CHECK_BOUNDS;
+#else
+    return 0;
+#endif
+}
+
 const char *ssm_status_str(int s) {
     switch (s) {
     case SSM_OK: return "SSM_OK";
@@ -592,6 +625,7 @@ const char *ssm_status_str(int s) {
     case SSM_ENONFINITE: return "SSM_ENONFINITE: non-finite particle state";
     case SSM_ETIMEOUT: return "SSM_ETIMEOUT: bounded device wait gave up";
     case SSM_ESTATE: return "SSM_ESTATE: call not valid in the current state";
+    case SSM_EBOUNDS: return "SSM_EBOUNDS: an index checked by the debug build fell outside its array";
     }
     return "unknown ssm_status";
 }

@@ -34,6 +34,7 @@
 namespace ssm {
 cudaError_t launch_init_x0_raw(int d, double *x, int64_t N, int64_t Np, uint64_t seed, double mean, double sd,
                                double *mpart, unsigned *ticket, double *mom, int *err, cudaStream_t st);
+SSM_BOUNDS_READER(bounds_hits_batch)
 }
 
 using namespace ssm;
@@ -172,7 +173,8 @@ kb_pair(BEns *ens, int n_ens, const BGlobal *g) {
         const int nc = NEWTON ? E.d + 1 : E.d;
         double *part = E.part + (int64_t)chunk * nc * E.Np;
         const int *act = NEWTON ? ((pass & 1) ? E.act1 : E.act0) : nullptr;
-        const int64_t ntgt = NEWTON ? (int64_t)E.cnt[pass] : E.N;
+        int64_t ntgt = NEWTON ? (int64_t)E.cnt[pass] : E.N;
+        if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= E.Np)) ntgt = 0;
         const double *src = NEWTON ? E.x : E.y;
         const double sc = NEWTON ? 1.0 : E.scale;
         if (E.d == 1) {
@@ -228,17 +230,19 @@ kb_update(BEns *ens, int n_ens, BGlobal *g, int kmax, int fp32, cudaGraphConditi
         const long long idx = base + threadIdx.x;
         bool keep = false;
         int e = 0, i = 0;
-        if (idx < total) {
+        if (idx < total && SSM_IN_BOUNDS(find_ens(pref, n_ens, idx) < n_ens)) {
             e = find_ens(pref, n_ens, idx);
             const BEns &E = ens[e];
             const int64_t t = idx - pref[e];
             i = ((pass & 1) ? E.act1 : E.act0)[t];
-            const int r = E.d == 1 ? update_one<1>(E, pass, t, i, fp32 != 0, kmax)
-                                   : update_one<3>(E, pass, t, i, fp32 != 0, kmax);
-            if (r == UPD_CONTINUE) keep = true;
-            else if (r == UPD_FLOOR) atomicAdd((unsigned long long *)&g->counters[CNT_FLOOR], 1ull);
-            else if (r == UPD_NOCONV) atomicOr(&g->err, ERR_NOCONV);
-            else if (r == UPD_NONFINITE) atomicOr(&g->err, ERR_NONFINITE);
+            if (SSM_IN_BOUNDS(i >= 0 && i < E.N)) {
+                const int r = E.d == 1 ? update_one<1>(E, pass, t, i, fp32 != 0, kmax)
+                                       : update_one<3>(E, pass, t, i, fp32 != 0, kmax);
+                if (r == UPD_CONTINUE) keep = true;
+                else if (r == UPD_FLOOR) atomicAdd((unsigned long long *)&g->counters[CNT_FLOOR], 1ull);
+                else if (r == UPD_NOCONV) atomicOr(&g->err, ERR_NOCONV);
+                else if (r == UPD_NONFINITE) atomicOr(&g->err, ERR_NONFINITE);
+            }
         }
         // append survivors to their ensemble's next list; lanes of one ensemble
         // share one atomic
@@ -538,6 +542,7 @@ ssm_status harvest_batch(ssm_batch *b) {
     if (e != cudaSuccess) { b->status = SSM_ECUDA; return SSM_ECUDA; }
     if (err & ERR_NONFINITE) b->status = SSM_ENONFINITE;
     else if (err & ERR_NOCONV) b->status = SSM_ENOCONV;
+    else if (bounds_hits_all()) b->status = SSM_EBOUNDS;
     return (ssm_status)b->status;
 }
 

@@ -20,7 +20,8 @@ k_pair(const double *__restrict__ src, const double *__restrict__ tgt, const int
        const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
        double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
     if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    const int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;   // block-uniform
     const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
@@ -35,7 +36,8 @@ k_pair2(const double *__restrict__ src, const double *__restrict__ tgt, const in
         const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
         double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
     if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    const int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;
     const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
@@ -51,7 +53,8 @@ k_pair2x(const double *__restrict__ src, const double *__restrict__ tgt, const i
          const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
          double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
     if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    const int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    int64_t ntgt = act ? (int64_t)(*cnt) : N;
+    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
     const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
     if (t0 >= ntgt) return;
     const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
@@ -196,5 +199,7 @@ int pair_shape_candidates(int kind, bool fp32, int (*out)[3], int max_out) {
     }
     return n;
 }
+
+SSM_BOUNDS_READER(bounds_hits_pair)
 
 }  // namespace ssm

@@ -305,7 +305,7 @@ template <int D>
 __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
                                int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
                                const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np,
-                               int *__restrict__ dpass) {
+                               int *__restrict__ dpass, int inject) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
 #pragma unroll
@@ -319,6 +319,12 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
         for (int k = 0; k < 16; ++k) hist[k] = 0;
         for (int k = 0; k < 4 * D; ++k) mom_prev[k] = mom[k];
         *dpass = 0;
+#ifdef SSM_CHECK_BOUNDS
+        // ssm_opts.inject = 1 (debug builds, N not a multiple of 128): list entry 0
+        // names particle N, past the particles but inside the padded arrays, for
+        // the bounds checks to catch
+        if (inject == 1) act[0] = (int)N;
+#endif
     }
 }
 
@@ -348,10 +354,12 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__res
     if (threadIdx.x == 0) { nrestart = 0; nfloor = 0; }
     __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n_in = *cnt_in;
+    int64_t n_in = *cnt_in;
+    if (t == 0 && !SSM_IN_BOUNDS(n_in >= 0 && n_in <= N)) n_in = 0;
+    if (!(n_in >= 0 && n_in <= N)) n_in = 0;
     bool keep = false;
     int i = 0;
-    if (t < n_in) {
+    if (t < n_in && SSM_IN_BOUNDS(act_in[t] >= 0 && act_in[t] < N)) {
         i = act_in[t];
         double S[D], Sw = 0.0, Y[D], X[D];
 #pragma unroll
@@ -807,10 +815,12 @@ cudaError_t launch_mm_implicit(ssm_ctx *c) {
 cudaError_t launch_newton_begin(ssm_ctx *c) {
     if (c->d == 1)
         k_newton_begin<1><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
-                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass);
+                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass,
+                                                              c->opt.inject);
     else
         k_newton_begin<3><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
-                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass);
+                                                              c->mom, c->mom_prev, c->N, c->Np, c->dpass,
+                                                              c->opt.inject);
     return cudaGetLastError();
 }
 
@@ -912,5 +922,7 @@ cudaError_t launch_normals32(uint64_t seed, int d, int64_t N, uint32_t step, uin
     else k_normals32<3><<<gs_blocks(N, 256), 256, 0, st>>>(seed, N, step, stream, out);
     return cudaGetLastError();
 }
+
+SSM_BOUNDS_READER(bounds_hits_particle)
 
 }  // namespace ssm

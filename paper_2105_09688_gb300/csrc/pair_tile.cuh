@@ -36,6 +36,14 @@ template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
 template <> struct V4<double> { using t = double4_32a; };
 
+// Particle of target slot t (0 for slots past ntgt).  Debug builds check the list
+// entry against the arrays' extent Np (SSM_CHECK_BOUNDS: recorded, slot 0 read instead).
+__device__ __forceinline__ int64_t target_index(const int *__restrict__ act, int64_t t, int64_t ntgt, int64_t Np) {
+    if (t >= ntgt) return 0;
+    const int64_t i = act ? (int64_t)act[t] : t;
+    return SSM_IN_BOUNDS(i >= 0 && i < Np) ? i : 0;
+}
+
 template <int KIND> struct KindInfo;
 template <> struct KindInfo<PK_DRIFT1> { static constexpr int D = 1, NC = 1; };
 template <> struct KindInfo<PK_DRIFT3> { static constexpr int D = 3, NC = 3; };
@@ -142,7 +150,7 @@ __device__ __forceinline__ void tile_scalar(const double *__restrict__ src, cons
     for (int r = 0; r < R; ++r) {
         const int64_t t = t0 + r * THREADS + tid;
         int64_t i = 0;
-        if (t < ntgt) i = act ? (int64_t)act[t] : t;
+        if (t < ntgt) i = target_index(act, t, ntgt, Np);
         tx[r] = cvt<T>(tgt[i], scale);
         ty[r] = D == 3 ? cvt<T>(tgt[Np + i], scale) : T(0);
         tz[r] = D == 3 ? cvt<T>(tgt[2 * Np + i], scale) : T(0);
@@ -294,9 +302,7 @@ template <int KIND> struct PackedInfo;   // accumulators per target: difference 
 template <> struct PackedInfo<PK_NEWTON3> { static constexpr int NC = 4, NX = 4; };
 template <> struct PackedInfo<PK_DRIFT3> { static constexpr int NC = 3, NX = 4; };
 
-__device__ __forceinline__ int64_t target_index(const int *__restrict__ act, int64_t t, int64_t ntgt) {
-    return t < ntgt ? (act ? (int64_t)act[t] : t) : 0;
-}
+
 
 // The two-sum compensation accumulators (hi, lo) of a thread's R2 x NC float2 sums,
 // folded once per SUB sources: in registers, or in shared memory (SMEM), where they
@@ -378,7 +384,7 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const f
         float v[2][3];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt);
+            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt, Np);
             v[e][0] = -(float)(tgt[i] * scale);
             v[e][1] = -(float)(tgt[Np + i] * scale);
             v[e][2] = -(float)(tgt[2 * Np + i] * scale);
@@ -459,7 +465,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         float v[2][4];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt);
+            const int64_t i = target_index(act, t0 + (2 * k + e) * THREADS + tid, ntgt, Np);
             const float a = (float)((tgt[i] - cc[0]) * scale), b = (float)((tgt[Np + i] - cc[1]) * scale),
                         d = (float)((tgt[2 * Np + i] - cc[2]) * scale);
             v[e][0] = usign * a;
@@ -521,7 +527,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         for (int e = 0; e < 2; ++e) {
             const int64_t t = t0 + (2 * k + e) * THREADS + tid;
             if (t < ntgt) {
-                const int64_t i = act ? (int64_t)act[t] : t;
+                const int64_t i = target_index(act, t, ntgt, Np);
                 double S[NX];
 #pragma unroll
                 for (int c = 0; c < NX; ++c) S[c] = comp.value(k, c, e);
@@ -578,7 +584,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
         for (int r = 0; r < R; ++r) {
             const int64_t t = t0 + r * THREADS + tid;
             if (t < ntgt) {
-                const int64_t i = act ? (int64_t)act[t] : t;
+                const int64_t i = target_index(act, t, ntgt, Np);
                 m[0] += tgt[i];
                 m[1] += tgt[Np + i];
                 m[2] += tgt[2 * Np + i];
@@ -606,7 +612,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
         for (int r = 0; r < R; ++r) {
             const int64_t t = t0 + r * THREADS + tid;
             if (t < ntgt) {
-                const int64_t i = act ? (int64_t)act[t] : t;
+                const int64_t i = target_index(act, t, ntgt, Np);
                 const double a = (tgt[i] - cc[0]) * scale, b = (tgt[Np + i] - cc[1]) * scale,
                              d = (tgt[2 * Np + i] - cc[2]) * scale;
                 ok &= (a * a + b * b + d * d <= (double)EXP_R2) ? 1 : 0;   // false for NaN

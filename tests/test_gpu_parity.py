@@ -374,6 +374,31 @@ def test_graph_replay_equals_single_steps_and_resume_is_bit_exact(S):
         s.close()
 
 
+@pytest.mark.parametrize("learned", [False, True])
+def test_device_pass_loop_equals_fixed_pass_launches(S, learned):
+    """The step-1 passes as a device-driven conditional graph node (default) and as a
+    fixed sequence of newton_kmax pass launches (ssm_opts.fixed_pass_launches) run the
+    same kernels on the same data: bit-identical states and equal work counters."""
+    N, h, K = 3000, 2.0 ** -8, 5
+    prec = S.SSM_FP32C_LEARNED if learned else S.SSM_FP32C
+    out = []
+    for fixed in (0, 1):
+        s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=13, precision=prec,
+                  fixed_pass_launches=fixed)
+        if learned:
+            S.load_ws(s)
+        s.step()                      # ssm_step and ssm_run_steps share the step graph
+        s.run_steps(K - 1)
+        x, n = s.get_state()
+        st = s.stats()
+        s.close()
+        out.append((x, n, st))
+    (xa, na, sa), (xb, nb, sb) = out
+    assert na == nb == K and np.array_equal(xa, xb)
+    for k in ("newton_passes", "newton_rows", "fallbacks", "floor_accepts", "max_passes"):
+        assert sa[k] == sb[k], k
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_drift_stage_is_antisymmetric(S, prec):
     N = 3000
