@@ -509,6 +509,19 @@ def main():
                 "kernel_ms": t_dom * 1e3, "other_pair_kernel_ms": (t_drift if dom == 0 else t_newton) * 1e3,
                 "other_pair_kernel_frac": FLOPS_PAIR[1 - dom] * N_PART * N_PART
                 / (t_drift if dom == 0 else t_newton) / 1e12 / peak}
+    # the FP32 pipes measured on this device (ssm_pipe_probe), and the FMA-pipe
+    # occupancy of the dominant kernel against the measured packed-FFMA2 rate: the
+    # centred expansion issues 8 FMA lane operations a pair (step 1: q in 4, the
+    # weighted sums in 4; drift: 3 + 4) as FFMA2
+    try:
+        pipes = S.ssm_pipe_probe()
+        fma_ops = {0: 8.0, 1: 7.0}[dom] if dom_form == 2 else None
+        cap = pipes["ffma2"] * n_sms * pipes["clock_ghz"] * 1e9
+        roofline["measured_pipes"] = dict(pipes, unit="FP32 lane operations per clock per SM")
+        roofline["measured_ffma2_tflops"] = 2.0 * cap / 1e12
+        roofline["fma_pipe_frac_of_measured_ffma2"] = (fma_ops * N_PART * N_PART / t_dom / cap) if fma_ops else None
+    except S.SSMError as e:
+        roofline["measured_pipes"] = {"error": str(e)}
 
     # end to end through the C ABI: pinned host state in, step, pinned host state out
     xh = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()

@@ -218,6 +218,16 @@ void ssm_destroy(ssm_ctx *ctx);
 /* Human-readable name of a status code. */
 const char *ssm_status_str(int status);
 
+/* Measured throughput of the FP32 pipes on the current device (no counterpart in the
+ * paper; a roofline basis for the pair sums): out[0..3] = FP32 lane operations per
+ * clock per SM of a sustained stream of FFMA, packed FFMA2, MUFU reciprocal
+ * (rcp.approx) and MUFU base-2 exponential (ex2.approx), each on eight independent
+ * register chains per thread over eight 256-thread blocks per SM; out[4] = the SM
+ * clock in GHz during the runs (clock64 against the global timer).  Synchronous,
+ * on the default stream, a few milliseconds; allocates and frees a small buffer.
+ * out: caller-owned host array of 5 doubles. */
+ssm_status ssm_pipe_probe(double *out);
+
 /* Build variant of the loaded library: a bit set of SSM_BUILD_* (0 = release).
  * SSM_BUILD_CHECK_BOUNDS: compiled with SSM_CHECK_BOUNDS, the debug build whose
  * kernels check the indices they take from data (active lists, counts, ensemble

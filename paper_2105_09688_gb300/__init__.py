@@ -23,7 +23,7 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_normals_fp32", "ssm_convert_check", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "ssm_drift_noalloc", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "SSM_COEF_GLSTAB", "ssm_stability_beta", "load_ws",
+    "ssm_set_plan", "ssm_drift_noalloc", "ssm_pipe_probe", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "SSM_COEF_GLSTAB", "ssm_stability_beta", "load_ws",
     "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
     "ssm_ws_num_params",
 ]
@@ -90,6 +90,7 @@ _SIGS = {
     "ssm_destroy": (None, [_vp]),
     "ssm_status_str": (ctypes.c_char_p, [_i32]),
     "ssm_build_flags": (_i32, []),
+    "ssm_pipe_probe": (_i32, [_DP]),
     "ssm_philox": (_i32, [_u64, _U32P, _i64, _U32P]),
     "ssm_normals": (_i32, [_u64, _i32, _i64, _i64, _i32, _DP]),
     "ssm_normals_fp32": (_i32, [_u64, _i32, _i64, _i64, _i32, ctypes.POINTER(ctypes.c_float)]),
@@ -400,6 +401,15 @@ def ssm_stability_beta(Lv, Lvt, Lb, Lbt, Ls, Lst, h):
     _check(lib().ssm_stability_beta(float(Lv), float(Lvt), float(Lb), float(Lbt), float(Ls), float(Lst), float(h),
                                     ctypes.byref(out)), "ssm_stability_beta")
     return float(out.value)
+
+
+def ssm_pipe_probe():
+    """Measured FP32 pipe rates of the current device: dict of lane operations per clock
+    per SM (ffma, ffma2, rcp, ex2) and the SM clock in GHz during the probe."""
+    out = np.zeros(5)
+    _check(lib().ssm_pipe_probe(_dp(out)), "ssm_pipe_probe")
+    return {"ffma": float(out[0]), "ffma2": float(out[1]), "rcp": float(out[2]), "ex2": float(out[3]),
+            "clock_ghz": float(out[4])}
 
 
 def ssm_convert_check(values):

@@ -137,8 +137,10 @@ Plan make_plan_shape(int64_t N, int kind, int vec2, int threads, int rpt, int fo
         if (chunks > cap) chunks = cap;
     }
     if (chunks < 1) chunks = 1;
+    // chunks are whole sub-tiles of the kernel (512 sources for the packed step-1 sums)
+    const int64_t sub = (kind == PK_NEWTON3 && vec2) ? 512 : SUB;
     int64_t len = (N + chunks - 1) / chunks;
-    len = (len + SUB - 1) / SUB * SUB;
+    len = (len + sub - 1) / sub * sub;
     p.chunk_len = len;
     p.chunks = (int)((N + len - 1) / len);
     return p;

@@ -298,14 +298,18 @@ template <> __device__ __forceinline__ void pair2x<PK_DRIFT3>(float2 sx, float2 
 // 2^(-|s|^2 + 2 s.t) <= 2^|t|^2 far from FP32 overflow.
 constexpr float EXP_R2 = 64.f;
 
-template <int KIND> struct PackedInfo;   // accumulators per target: difference / expanded form
-template <> struct PackedInfo<PK_NEWTON3> { static constexpr int NC = 4, NX = 4; };
-template <> struct PackedInfo<PK_DRIFT3> { static constexpr int NC = 3, NX = 4; };
+// Accumulators per target (difference / expanded form) and sources per shared-memory
+// sub-tile of the packed kinds: the step-1 sums stage 512 sources at a time (half the
+// barriers and two-sum folds of 256: 19.90 against 20.15 ms a pass at N = 2^18), the
+// drift 256 (17.91 against 18.02 ms).
+template <int KIND> struct PackedInfo;
+template <> struct PackedInfo<PK_NEWTON3> { static constexpr int NC = 4, NX = 4, SUBP = 512; };
+template <> struct PackedInfo<PK_DRIFT3> { static constexpr int NC = 3, NX = 4, SUBP = 256; };
 
 
 
 // The two-sum compensation accumulators (hi, lo) of a thread's R2 x NC float2 sums,
-// folded once per SUB sources: in registers, or in shared memory (SMEM), where they
+// folded once per sub-tile of sources: in registers, or in shared memory (SMEM), where they
 // leave the registers to the inner loop's accumulators and targets (more resident
 // blocks).  Shared layout slot-major, hl[(2 slot + {0: hi, 1: lo}) THREADS + tid],
 // slot = (k NC + c) 2 + lane: a warp's accesses fall in distinct banks.
@@ -367,15 +371,15 @@ __host__ __device__ constexpr bool comp_in_smem(int threads, int r) {
     return r <= 4 && threads * (r / 2) * 4 * 4 * 4 <= 32768;
 }
 
-// Difference form of a packed tile (buf: 2*SUB float4 of shared memory).
+// Difference form of a packed tile (buf: 2 SUBP float4 of shared memory).
 template <int KIND, int THREADS, int R>
 __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                  const double *__restrict__ tgt, const int *__restrict__ act,
                                                  int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
                                                  double scale, double *__restrict__ part) {
-    constexpr int NC = PackedInfo<KIND>::NC, R2 = R / 2;
+    constexpr int NC = PackedInfo<KIND>::NC, R2 = R / 2, SUBP = PackedInfo<KIND>::SUBP;
     float4 *sxy = buf;                              // (x, x, y, y)
-    float2 *szz = reinterpret_cast<float2 *>(buf + SUB);   // (z, z)
+    float2 *szz = reinterpret_cast<float2 *>(buf + SUBP);   // (z, z)
     const int tid = threadIdx.x;
 
     float2 ntx[R2], nty[R2], ntz[R2];
@@ -400,8 +404,8 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const f
         for (int c = 0; c < NC; ++c) acc[k][c] = f2(0.f, 0.f);
     Comp<R2, NC, THREADS, comp_in_smem(THREADS, R)> comp(hl, tid);
 
-    for (int64_t base = j0; base < j1; base += SUB) {
-        const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
+    for (int64_t base = j0; base < j1; base += SUBP) {
+        const int ns = (int)((j1 - base) < SUBP ? (j1 - base) : SUBP);
         __syncthreads();
         for (int s = tid; s < ns; s += THREADS) {
             const int64_t j = base + s;
@@ -411,9 +415,9 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const f
         }
         __syncthreads();
         const float2 one = *s_one;
-        if (ns == SUB) {
+        if (ns == SUBP) {
 #pragma unroll 4
-            for (int s = 0; s < SUB; ++s) {
+            for (int s = 0; s < SUBP; ++s) {
                 const float4 a = sxy[s];
                 const float2 b = szz[s];
 #pragma unroll
@@ -455,7 +459,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
                                                 int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
                                                 double scale, const double (&cc)[3], double *__restrict__ part) {
     constexpr bool NEWTON = KIND == PK_NEWTON3;
-    constexpr int NX = PackedInfo<KIND>::NX, R2 = R / 2;
+    constexpr int NX = PackedInfo<KIND>::NX, R2 = R / 2, SUBP = PackedInfo<KIND>::SUBP;
     const int tid = threadIdx.x;
     const float usign = NEWTON ? -2.f : 2.f;
 
@@ -485,8 +489,8 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         for (int c = 0; c < NX; ++c) acc[k][c] = f2(0.f, 0.f);
     Comp<R2, NX, THREADS, comp_in_smem(THREADS, R)> comp(hl, tid);
 
-    for (int64_t base = j0; base < j1; base += SUB) {
-        const int ns = (int)((j1 - base) < SUB ? (j1 - base) : SUB);
+    for (int64_t base = j0; base < j1; base += SUBP) {
+        const int ns = (int)((j1 - base) < SUBP ? (j1 - base) : SUBP);
         __syncthreads();
         for (int s = tid; s < ns; s += THREADS) {
             const int64_t j = base + s;
@@ -499,11 +503,11 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
         }
         __syncthreads();
         const float2 one = *s_one;
-        if (ns == SUB) {
+        if (ns == SUBP) {
 // unroll timed at N = 2^18: 128 x 4 step-1 pass 20.35 ms unrolled 16 (20.53 ms at 8);
 // 128 x 8 drift pass 17.50 ms unrolled 12 (17.67 ms at 8, 17.78 ms at 16)
 #pragma unroll (NEWTON && R == 4 ? 16 : (!NEWTON && R == 8) ? 12 : 8)
-            for (int s = 0; s < SUB; ++s) {
+            for (int s = 0; s < SUBP; ++s) {
                 const float4 a = buf[2 * s], b = buf[2 * s + 1];
 #pragma unroll
                 for (int k = 0; k < R2; ++k)
@@ -571,7 +575,7 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
                                             int64_t j1, int64_t t0, double scale, double *__restrict__ part) {
     static_assert(R % 2 == 0, "targets per thread come in pairs");
     static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
-    __shared__ float4 buf[2 * SUB];
+    __shared__ float4 buf[2 * PackedInfo<KIND>::SUBP];
     __shared__ float s_hl[comp_in_smem(THREADS, R) ? THREADS * (R / 2) * 4 * 4 : 1];
     __shared__ float2 s_one;
     __shared__ double s_red[THREADS / 32][4];
