@@ -755,7 +755,10 @@ ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
         }
         // Then the chunk count of the fastest shape: 1.5, 2 and 2.5 times the planned
         // count (finer work items balance the last wave better; measured at N = 2^18,
-        // 128 x 8 drift: 17.9 ms with 7 chunks, 17.6 ms with 16).
+        // 128 x 8 drift: 17.9 ms with 7 chunks, 17.6 ms with 16).  Every chunk adds a
+        // set of partial sums that is written to memory and read back by the
+        // consumer, so a larger count is kept only when it is faster by more than
+        // 0.5%.
         if (c->opt.tile_chunks <= 0) {
             const Plan base = best;
             const int cap = chunks_cap(c->N, kind_nc(kind));
@@ -764,7 +767,11 @@ ssm_status ssm_autotune(ssm_ctx *c, double *best_ms) {
                 if (ch > cap) ch = cap;
                 if (ch <= base.chunks) continue;
                 const Plan p = make_plan_shape(c->N, kind, base.vec2, base.threads, base.rpt, ch, 0);
-                if (p.chunks != base.chunks) try_plan(p);
+                if (p.chunks == base.chunks) continue;
+                const Plan keep = best;
+                const float keep_t = best_t;
+                try_plan(p);
+                if (best.chunks == p.chunks && !(best_t < 0.995f * keep_t)) { best = keep; best_t = keep_t; }
             }
         }
         if (q == 0) c->plan_newton = best; else c->plan_drift = best;

@@ -157,13 +157,14 @@ k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__
             double g[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c];
-            const double a = 1.0 + h * uu;
+            const double a = 1.0 + h * uu, b = a + 2.0 * h * uu;
             const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
-            const double fct = 2.0 * h * ug / (a + 2.0 * h * uu);
+            const double r = 1.0 / (a * b);   // one FP64 division for 1/a and 1/b
+            const double ia = b * r, fct = 2.0 * h * ug * (a * r);
             double smax = 0.0, umax = 1.0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double s = (g[c] - fct * u[c]) / a;
+                const double s = (g[c] - fct * u[c]) * ia;
                 u[c] -= s;
                 smax = fmax(smax, fabs(s));
                 umax = fmax(umax, fabs(u[c]));

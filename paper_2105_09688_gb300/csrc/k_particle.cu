@@ -579,8 +579,9 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // grid, so that runs at different h share one Brownian path.
 // ---------------------------------------------------------------------------
 // FP32C form (F32): dW from the FP32 transform, the increment h b + sigma dW in FP32
-// added to the FP64 state with one FP64 add, and the moments from FP32 powers in
-// Kahan-compensated FP32 per thread (FP64 across threads and blocks).  FP64 form:
+// added to the FP64 state with one FP64 add, and the moments from FP32 powers summed
+// in FP32 over 32 particles and in FP64 beyond (per thread, then across threads and
+// blocks).  FP64 form:
 // all FP64.  Compiled for eul_min_blocks<D> resident blocks per SM (3 at d = 2 and
 // 3, whose FP32C forms need more than 64 registers a thread; 4 at d = 1) and
 // launched on that many blocks per SM, one wave.
@@ -628,7 +629,7 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
                 if (!GEN) hb[c] = OU ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
             }
 #pragma unroll
-            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32(yv[c]);
+            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32_trunc(yv[c]);
             if (GEN)
 #pragma unroll
                 for (int c = 0; c < D; ++c) hb[c] = hf * moment_b<float>(coef, c, yf, ymf, p0f, p1f);
@@ -646,18 +647,29 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
                 p[3 * D + c] = v2 * v2;
             }
         };
-        float mh[4 * D], ml[4 * D];
+        // the powers are summed in FP32 over 32 particles at a time (error < 32 eps of
+        // their absolute sum) and those sums added in FP64 into this thread's slots in
+        // shared memory (fewer registers and instructions than a compensated sum per
+        // particle)
+        __shared__ double msum[4 * D][EUL_THREADS];
+        float ms[4 * D];
 #pragma unroll
-        for (int k = 0; k < 4 * D; ++k) { mh[k] = 0.0f; ml[k] = 0.0f; }
+        for (int k = 0; k < 4 * D; ++k) { ms[k] = 0.0f; msum[k][threadIdx.x] = 0.0; }
+        int nb = 0;
 #pragma unroll 1
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
             float p[4 * D];
             advance(i, p);
 #pragma unroll
-            for (int k = 0; k < 4 * D; ++k) kahan_acc(mh[k], ml[k], p[k]);
+            for (int k = 0; k < 4 * D; ++k) ms[k] += p[k];
+            if (++nb == 32) {
+#pragma unroll
+                for (int k = 0; k < 4 * D; ++k) { msum[k][threadIdx.x] += (double)ms[k]; ms[k] = 0.0f; }
+                nb = 0;
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 4 * D; ++k) m[k] = (double)mh[k] - (double)ml[k];
+        for (int k = 0; k < 4 * D; ++k) m[k] = msum[k][threadIdx.x] + (double)ms[k];
     } else {
         double ym[D];
 #pragma unroll

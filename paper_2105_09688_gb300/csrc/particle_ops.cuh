@@ -53,12 +53,17 @@ __device__ __forceinline__ void local_root(const double *S, double Sw, const dou
             g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c] + 0.5 * h * Sw * (u[c] - Y[c]);
             ug += u[c] * g[c];
         }
+        // Sherman-Morrison with both reciprocals from one division: 1/a = b/(ab),
+        // 1/b = a/(ab), b = a + 2h|u|^2 (an FP64 division is a long sequence on
+        // the FP64 pipe, the slow pipe of this part)
         const double a = 1.0 + h * uu + 0.5 * h * Sw;
-        const double f = 2.0 * h * ug / (a + 2.0 * h * uu);
+        const double b = a + 2.0 * h * uu;
+        const double r = 1.0 / (a * b);
+        const double ia = b * r, f = 2.0 * h * ug * (a * r);
         double smax = 0.0, umax = 1.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const double s = (g[c] - f * u[c]) / a;
+            const double s = (g[c] - f * u[c]) * ia;
             u[c] -= s;
             smax = fmax(smax, fabs(s));
             umax = fmax(umax, fabs(u[c]));
