@@ -94,7 +94,7 @@ typedef enum { SSM_COEF_CUBIC1D_GAUSS = 0, SSM_COEF_COUPLED3D = 1, SSM_COEF_OU =
  *      double.  Step 2 draws the same Philox words but evaluates the Box-Muller
  *      transform in FP32 (|z error| < 5e-6) and forms the increment h b + sigma dW
  *      in FP32 before adding it to the FP64 state; the moments are FP32 powers
- *      summed in compensated (Kahan) FP32 per thread and in double across threads.
+ *      summed in FP32 over 32 particles and in double beyond.
  *      X_0 is drawn in FP64 in both forms.
  *  SSM_FP32C_LEARNED: SSM_FP32C with a learned initial guess for step 1
  *      (SSM_COEF_COUPLED3D only; load weights with ssm_ws_load). */

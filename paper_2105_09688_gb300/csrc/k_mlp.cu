@@ -129,7 +129,44 @@ __device__ __forceinline__ void forward(const Net &n, const float *f, float *out
     }
 }
 
-// Learned start of step 1: Y^0_i = root of u = X_i + h(-u|u|^2 + 0.5 S_pred).
+// The start from the predicted pair sum: Y^0 = X + delta with delta the root of
+// delta = h(-(X + delta)|X + delta|^2 + 0.5 S_pred), by Newton in FP32 on delta (the
+// Jacobian a I + 2h u u^T, u = X + delta, inverted by Sherman-Morrison with one
+// reciprocal for 1/a and 1/(a + 2h|u|^2)); FP32 on the small increment is far more
+// accurate than the start needs (the prediction itself is good to ~1e-6), and the FP64
+// state keeps X exact.  A non-finite result leaves the plain start Y = X.
+__device__ __forceinline__ void cubic_start(const double (&X)[3], const float (&S)[3], double h, double *yi,
+                                            int64_t Np) {
+    const float hf = (float)h;
+    float xf[3], s2[3], dl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { xf[c] = f64_to_f32_fast(X[c]); s2[c] = 0.5f * hf * S[c]; dl[c] = 0.0f; }
+    for (int it = 0; it < 10; ++it) {
+        float u[3], g[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = xf[c] + dl[c];
+        const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] = dl[c] + hf * u[c] * uu - s2[c];
+        const float a = 1.0f + hf * uu, b = a + 2.0f * hf * uu;
+        const float r = 1.0f / (a * b);
+        const float ia = b * r, f = 2.0f * hf * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2]) * (a * r);
+        float smax = 0.0f, dmax = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float st = (g[c] - f * u[c]) * ia;
+            dl[c] -= st;
+            smax = fmaxf(smax, fabsf(st));
+            dmax = fmaxf(dmax, fabsf(dl[c]));
+        }
+        if (smax <= 1e-7f * dmax) break;
+    }
+    if (isfinite(dl[0]) && isfinite(dl[1]) && isfinite(dl[2]))
+#pragma unroll
+        for (int c = 0; c < 3; ++c) yi[c * Np] = X[c] + f32_to_f64(dl[c]);
+}
+
+// Learned start of step 1 on the CUDA cores (FFMA, weights broadcast from shared memory).
 __global__ void __launch_bounds__(128)
 k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__restrict__ blob,
            const double *__restrict__ mom, int64_t N, int64_t Np, double h) {
@@ -149,31 +186,145 @@ k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__
         for (int k = 0; k < NI; ++k) f[k] = (f[k] - n.fm[k]) / n.fs[k];
         float o[NO];
         forward<false>(n, f, o, nullptr, nullptr);
-        double S[3], u[3];
+        float S[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { S[c] = (double)(o[c] * n.ys[c] + n.ym[c]); u[c] = X[c]; }
-        for (int it = 0; it < 30; ++it) {   // Newton on the cubic; Jacobian a I + 2h u u^T (Sherman-Morrison)
-            const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            double g[3];
+        for (int c = 0; c < 3; ++c) S[c] = o[c] * n.ys[c] + n.ym[c];
+        cubic_start(X, S, h, y + i, Np);
+    }
+}
+
+// ---- the same start on the tensor cores: mma.sync m16n8k16, BF16 operands, FP32
+// accumulate -------------------------------------------------------------------------
+// A warp takes 32 particles at a time and pushes each 16-particle half through the four
+// layers: activations [16 x K] are the A operand, the stored BF16 weights (row-major
+// [out][in], i.e. the B operand in column order) are read from shared memory, the
+// FP32 accumulators get bias and SiLU and are rounded to BF16 pairs that are, register
+// for register, the A operand of the next layer (the m16n8 accumulator layout of two
+// adjacent n-tiles is the m16k16 operand layout).  Rows of W are padded by 8 elements
+// so that the fragment loads of a warp fall in distinct banks.
+constexpr int MW_LD1 = NI + 8, MW_LD = NH + 8;
+constexpr int MW_W2 = NH * MW_LD1, MW_W3 = MW_W2 + NH * MW_LD, MW_W4 = MW_W3 + NH * MW_LD, MW_TOT = MW_W4 + 8 * MW_LD;
+constexpr int MMA_WARPS = 4;
+struct MmaNet {
+    __nv_bfloat16 w[MW_TOT];                          // W1 | W2 | W3 | W4 (8 rows; rows 3..7 zero)
+    float b1[NH], b2[NH], b3[NH], b4[8];
+    float fm[NI], fsi[NI], ym[4], ys[4];
+    __nv_bfloat16 feat[MMA_WARPS][32][NI + 8];        // a warp's staged, standardised features
+    float out[MMA_WARPS][32][4];                      // a warp's network outputs
+};
+
+__device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); }
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float silu_fast(float s) { return s * rcp_approx(1.0f + ex2_approx(-1.4426950408889634f * s)); }
+
+// One hidden layer: d[j] = A . W^T for the 8 n-tiles of 64 outputs (KT k-tiles of
+// input), then bias + SiLU, repacked in place as the next layer's 4 k-tiles.
+template <int KT>
+__device__ __forceinline__ void mma_hidden(const __nv_bfloat16 *W, int ld, const float *bias, unsigned (&a)[4][4],
+                                           int g, int t) {
+    float d[8][4];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] = u[c] - X[c] + h * u[c] * uu - 0.5 * h * S[c];
-            const double a = 1.0 + h * uu, b = a + 2.0 * h * uu;
-            const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
-            const double r = 1.0 / (a * b);   // one FP64 division for 1/a and 1/b
-            const double ia = b * r, fct = 2.0 * h * ug * (a * r);
-            double smax = 0.0, umax = 1.0;
+    for (int j = 0; j < 8; ++j) {
+        d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.0f;
+        const __nv_bfloat16 *row = W + (8 * j + g) * ld + 2 * t;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double s = (g[c] - fct * u[c]) * ia;
-                u[c] -= s;
-                smax = fmax(smax, fabs(s));
-                umax = fmax(umax, fabs(u[c]));
+        for (int kk = 0; kk < KT; ++kk) mma_bf16(d[j], a[kk], lds32(row + 16 * kk), lds32(row + 16 * kk + 8));
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float c0 = bias[8 * j + 2 * t], c1 = bias[8 * j + 2 * t + 1];
+        const unsigned lo = pack_bf16(silu_fast(d[j][0] + c0), silu_fast(d[j][1] + c1));
+        const unsigned hi = pack_bf16(silu_fast(d[j][2] + c0), silu_fast(d[j][3] + c1));
+        a[j >> 1][(j & 1) * 2 + 0] = lo;
+        a[j >> 1][(j & 1) * 2 + 1] = hi;
+    }
+}
+
+__global__ void __launch_bounds__(MMA_WARPS * 32)
+k_ws_start_mma(const double *__restrict__ x, double *__restrict__ y, const float *__restrict__ blob,
+               const double *__restrict__ mom, int64_t N, int64_t Np, double h) {
+    __shared__ MmaNet sm;
+    const __nv_bfloat16 *wg = reinterpret_cast<const __nv_bfloat16 *>(blob + OFF_W);
+    for (int k = threadIdx.x; k < NW1; k += blockDim.x) sm.w[(k / NI) * MW_LD1 + k % NI] = wg[k];
+    for (int k = threadIdx.x; k < NW2; k += blockDim.x) sm.w[MW_W2 + (k / NH) * MW_LD + k % NH] = wg[NW1 + k];
+    for (int k = threadIdx.x; k < NW3; k += blockDim.x) sm.w[MW_W3 + (k / NH) * MW_LD + k % NH] = wg[NW1 + NW2 + k];
+    for (int k = threadIdx.x; k < 8 * NH; k += blockDim.x)
+        sm.w[MW_W4 + (k / NH) * MW_LD + k % NH] = k < NO * NH ? wg[NW1 + NW2 + NW3 + k] : __float2bfloat16_rn(0.0f);
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+        sm.b1[k] = blob[OFF_B1 + k];
+        sm.b2[k] = blob[OFF_B2 + k];
+        sm.b3[k] = blob[OFF_B3 + k];
+    }
+    if (threadIdx.x < 8) sm.b4[threadIdx.x] = threadIdx.x < NO ? blob[OFF_B4 + threadIdx.x] : 0.0f;
+    if (threadIdx.x < 4) {
+        sm.ym[threadIdx.x] = blob[OFF_YMEAN + threadIdx.x];
+        sm.ys[threadIdx.x] = blob[OFF_YSTD + threadIdx.x];
+    }
+    if (threadIdx.x < NI) {
+        sm.fm[threadIdx.x] = blob[OFF_FMEAN + threadIdx.x];
+        sm.fsi[threadIdx.x] = 1.0f / blob[OFF_FSTD + threadIdx.x];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    __nv_bfloat16(*feat)[NI + 8] = sm.feat[warp];
+    float(*out)[4] = sm.out[warp];
+    for (int64_t base = ((int64_t)blockIdx.x * MMA_WARPS + warp) * 32; base < N;
+         base += (int64_t)gridDim.x * MMA_WARPS * 32) {
+        const int64_t i = base + lane;
+        double X[3] = {0.0, 0.0, 0.0};
+        if (i < N)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) X[c] = x[c * Np + i];
+        float f[NI];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = f64_to_f32_fast(X[c]);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) f[3 + k] = (float)mom[k];
+        f[15] = (float)h;
+#pragma unroll
+        for (int k = 0; k < NI; k += 2)
+            *reinterpret_cast<unsigned *>(&feat[lane][k]) =
+                pack_bf16((f[k] - sm.fm[k]) * sm.fsi[k], (f[k + 1] - sm.fm[k + 1]) * sm.fsi[k + 1]);
+        __syncwarp();
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = 16 * mt + g, r1 = r0 + 8;
+            unsigned a[4][4];
+            a[0][0] = lds32(&feat[r0][2 * t]);
+            a[0][1] = lds32(&feat[r1][2 * t]);
+            a[0][2] = lds32(&feat[r0][2 * t + 8]);
+            a[0][3] = lds32(&feat[r1][2 * t + 8]);
+            mma_hidden<1>(sm.w, MW_LD1, sm.b1, a, g, t);
+            mma_hidden<4>(sm.w + MW_W2, MW_LD, sm.b2, a, g, t);
+            mma_hidden<4>(sm.w + MW_W3, MW_LD, sm.b3, a, g, t);
+            float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const __nv_bfloat16 *row = sm.w + MW_W4 + g * MW_LD + 2 * t;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(o, a[kk], lds32(row + 16 * kk), lds32(row + 16 * kk + 8));
+            if (t < 2) {   // columns 2t, 2t + 1 of rows r0, r1 (outputs 0..2; column 3 is padding)
+                out[r0][2 * t] = o[0] + sm.b4[2 * t];
+                out[r0][2 * t + 1] = o[1] + sm.b4[2 * t + 1];
+                out[r1][2 * t] = o[2] + sm.b4[2 * t];
+                out[r1][2 * t + 1] = o[3] + sm.b4[2 * t + 1];
             }
-            if (smax <= 1e-16 * umax) break;
         }
-        if (isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))
+        __syncwarp();
+        if (i < N) {
+            float S[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) y[c * Np + i] = u[c];
+            for (int c = 0; c < 3; ++c) S[c] = out[lane][c] * sm.ys[c] + sm.ym[c];
+            cubic_start(X, S, h, y + i, Np);
+        }
+        __syncwarp();
     }
 }
 
@@ -382,12 +533,20 @@ cudaError_t set_smem_limits() {
     return e;
 }
 
+// The learned start on the form the context selects (ssm_opts.ws_forward): 0 =
+// tensor-core mma.sync, 1 = CUDA-core FFMA.
 cudaError_t ws_forward_start(ssm_ctx *c) {
-    cudaError_t e = set_smem_limits();
-    if (e != cudaSuccess) return e;
-    int64_t blocks = (c->N + 127) / 128;
-    if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
-    k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+    if (c->opt.ws_forward == 1) {
+        cudaError_t e = set_smem_limits();
+        if (e != cudaSuccess) return e;
+        int64_t blocks = (c->N + 127) / 128;
+        if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
+        k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+    } else {
+        int64_t blocks = (c->N + MMA_WARPS * 32 - 1) / (MMA_WARPS * 32);
+        if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
+        k_ws_start_mma<<<(unsigned)blocks, MMA_WARPS * 32, 0, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+    }
     return cudaGetLastError();
 }
 

@@ -629,7 +629,7 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
                 if (!GEN) hb[c] = OU ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
             }
 #pragma unroll
-            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32_trunc(yv[c]);
+            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32_fast(yv[c]);
             if (GEN)
 #pragma unroll
                 for (int c = 0; c < D; ++c) hb[c] = hf * moment_b<float>(coef, c, yf, ymf, p0f, p1f);
