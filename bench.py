@@ -572,6 +572,28 @@ def main():
                     "fallbacks": rst["fallbacks"], "floor_accepts": rst["floor_accepts"]}
         r.close()
 
+    # the learned start alone, its network forward on the tensor cores (mma.sync, BF16)
+    # and on the CUDA cores (FFMA, FP32), on the same state (the faster is the default)
+    ws_forward = None
+    if form.startswith("learned"):
+        ws_forward = {}
+        for fwd, name in ((0, "mma_sync_bf16"), (1, "ffma_fp32")):
+            q = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
+                      precision=S.SSM_FP32C_LEARNED, ws_forward=fwd)
+            S.load_ws(q)
+            q.run_steps(1)
+            q.pair_pass(2)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            stream.synchronize()
+            ev[0].record(stream)
+            for _ in range(5):
+                q.pair_pass(2)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            ws_forward[name + "_ms"] = ev[0].elapsed_time(ev[1]) / 5
+            q.close()
+        ws_forward["default"] = "mma_sync_bf16"
+
     # the same FP32C form without the learned start (same launch shapes, same timing)
     fp32c_plain = None
     if form.startswith("learned"):
@@ -678,6 +700,7 @@ def main():
             "measure_y_form": measure_y,
             "o_n_kernels": o_n,
             "full_run": full_run,
+            "learned_start_forward": ws_forward,
             "floor_accepts_per_step": (st1["floor_accepts"] - st0["floor_accepts"]) / args.steps,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

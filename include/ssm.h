@@ -129,6 +129,11 @@ typedef struct {
                                §1 contrasts with the SSM, solved by block-Jacobi passes (each
                                an O(N^2) pair pass at the common iterate) to newton_tol.
                                Not with SSM_FP32C_LEARNED. */
+    int ws_forward;         /* learned form: the network's forward in the start of step 1 on
+                               0 (default) the tensor cores (mma.sync m16n8k16, BF16 operands,
+                               FP32 accumulation) or 1 the CUDA cores (FFMA, FP32 activations);
+                               the default is the faster one measured (ssm_pair_pass(ctx, 2)
+                               times it) */
     int fixed_pass_launches; /* 0 (default): the passes of step 1 (coupled sets against mu^X)
                                run as a device-driven loop, a conditional node of the step's
                                CUDA graph that launches only passes with work.  1: the step
@@ -287,9 +292,12 @@ ssm_status ssm_cardano(const double *x, int64_t n, double h, double *y);
  *              and (1/N) sum_j w_ij, w_ij = 1/(1 + |X_j - Y_i|^2), for all N targets
  *              at the current Y (§2.3 eq. SSTM:scheme 1);
  *   which = 1: the step-2 drift pair sums b(Y_i, mu^Y) of the context's
- *              coefficient set (§2.3 eq. SSTM:scheme 2).
- * Overwrites only the context's partial-sum scratch (the state is untouched).
- * *pairs receives the number of pair evaluations enqueued (may be NULL). */
+ *              coefficient set (§2.3 eq. SSTM:scheme 2);
+ *   which = 2: the learned start of step 1 alone (SSM_FP32C_LEARNED with weights
+ *              loaded; no counterpart in the paper), from the current X into Y.
+ * Overwrites only the context's partial-sum scratch, or for which = 2 the stage Y
+ * (the state X is untouched).  *pairs receives the number of pair evaluations
+ * enqueued, 0 for which = 2 (may be NULL). */
 ssm_status ssm_pair_pass(ssm_ctx *ctx, int which, int64_t *pairs);
 
 /* Autotuner of the pair-sum launch shapes (no counterpart in the paper, whose

@@ -257,7 +257,9 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
         const double r = h / hf;
         if (r < 1.0 || fabs(nearbyint(r) - r) > 1e-9) return SSM_EINVAL;
     }
-    if (o.tile_chunks < 0 || o.fixed_pass_launches < 0 || o.fixed_pass_launches > 1) return SSM_EINVAL;
+    if (o.tile_chunks < 0 || o.fixed_pass_launches < 0 || o.fixed_pass_launches > 1 || o.ws_forward < 0 ||
+        o.ws_forward > 1)
+        return SSM_EINVAL;
     // ssm_opts.inject: only in the debug build, only the planted list entry of step 1
     // (coupled sets against mu^X) at an N whose padded arrays extend past particle N
 #ifdef SSM_CHECK_BOUNDS
@@ -694,11 +696,18 @@ ssm_status ssm_normals_fp32(uint64_t seed, int d, int64_t N, int64_t step, int s
 }
 
 ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
-    if (!c || (which != 0 && which != 1)) return SSM_EINVAL;
+    if (!c || which < 0 || which > 2) return SSM_EINVAL;
     if (c->status != SSM_OK) return (ssm_status)c->status;
     if (is_moment(c->coef) || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
+    if (which == 2 && !(c->prec == SSM_FP32C_LEARNED && c->ws_loaded)) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
     cudaError_t e;
+    if (which == 2) {
+        e = ws_forward_start(c);
+        if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
+        if (pairs) *pairs = 0;
+        return SSM_OK;
+    }
     if (which == 0) {
         e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, nullptr, nullptr, c->N, c->Np, 1.0,
                       c->part, c->st);

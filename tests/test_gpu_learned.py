@@ -143,3 +143,29 @@ def test_learned_form_without_weights_runs_plain(S):
     xp, _ = _run(S, N, seed, K, S.SSM_FP32C)
     xl, sl = _run(S, N, seed, K, S.SSM_FP32C_LEARNED)
     assert np.array_equal(xl, xp) and sl["fallbacks"] == 0
+
+
+def test_tensor_core_and_cuda_core_starts_agree(S):
+    """The learned start on the tensor cores (mma.sync, BF16 activations) and on the
+    CUDA cores (FFMA, FP32 activations), from the shipped network at N = 2^16: the two
+    starts differ by the BF16 rounding of the activations only (well below the
+    network's own error), and the steps that follow reach the same roots to the
+    residual tolerance with the same pass counts."""
+    N, K = 1 << 16, 3
+    starts, runs = [], []
+    for fwd in (0, 1):
+        s = S.SSM(d=3, N=N, h=H, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2, precision=S.SSM_FP32C_LEARNED,
+                  ws_forward=fwd)
+        S.load_ws(s)
+        s.pair_pass(2)                       # the learned start alone, from X_0 into Y
+        starts.append(s.get_stage(S.SSM_STAGE_Y))
+        s.run_steps(K)
+        x, _ = s.get_state()
+        runs.append((x, s.stats()))
+        s.close()
+    x0 = S.SSM(d=3, N=N, h=H, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=2).get_state()[0]
+    move = np.max(np.abs(starts[1] - x0))          # the start's own step away from X
+    assert move > 1e-3
+    assert np.max(np.abs(starts[0] - starts[1])) < 2e-5
+    assert np.max(np.abs(runs[0][0] - runs[1][0])) < K * 2 * 64 * 1e-10
+    assert runs[0][1]["newton_passes"] == runs[1][1]["newton_passes"]
