@@ -45,13 +45,13 @@ FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expan
 # N = 2^18, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for
 # each source-chunk count the autotuner can pick for that shape (the partial sums
 # written grow with it); valid only for the kernel sources they were measured on
-# (their SHA-256 below), otherwise the roofline's traffic is null.
+# (the tile code and its launchers, SHA-256 below), otherwise the roofline's traffic
+# is null.
 MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18),
-                    "bytes_by_chunks": {13: 13454336 + 50698240, 19: 13403136 + 100761344,
-                                        26: 13871104 + 159572736, 32: 15556608 + 210136320},
-                    "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu",
-                                "paper_2105_09688_gb300/csrc/ssm_device.cuh"),
-                    "sha256": "7c0f2251c02f24250a5a4bd9ad8ea2970848449d59a646a7dfc6c4d09257c704"}
+                    "bytes_by_chunks": {13: 13088000 + 48971008, 19: 15219968 + 100673536,
+                                        26: 16034304 + 159384576, 32: 15156480 + 209587968},
+                    "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu"),
+                    "sha256": "212ba0fddeb4208920fb05eb4488f1a560fb4d88749b4513c610cc826b9fbe73"}
 
 
 def measured_traffic(kernel, kind, threads, rpt, n, chunks):
