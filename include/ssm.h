@@ -395,8 +395,12 @@ void ssm_batch_destroy(ssm_batch *b);
  * weights, FP32 arithmetic) maps the features f = (x_i (3), the raw moments
  * m_k = (1/N) sum_j x_j^k, k = 1..4, per coordinate (12, k-major), h) of particle i
  * to the converged pair sum S(Y*_i) = (1/N) sum_j (X_j - Y*_i)/(1 + |X_j - Y*_i|^2);
- * step 1 then starts from the root of u = x_i + h(-u|u|^2 + S_pred/2) and runs the
- * usual passes.  A particle whose residual still exceeds newton_tol after
+ * step 1 then starts from the root of u = x_i + h(-u|u|^2 + S_start/2) and runs the
+ * usual passes, where S_start = S_pred plus, from the second step of a run on, the
+ * previous step's error S(Y*_i) - S_pred of the same particle (the part of S that
+ * the network cannot see -- the fluctuation of the particular sample of N particles
+ * about its law -- changes little in one step; ssm_set_state, ssm_ws_load and
+ * ssm_pair_pass(ctx, 2) drop the carried error for the next step).  A particle whose residual still exceeds newton_tol after
  * ssm_opts.ws_passes passes restarts from the plain start Y = X (plain Newton is
  * the judge); ssm_stats reports those restarts as fallbacks.
  *

@@ -154,7 +154,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, spred, wsprev, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -197,6 +197,8 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.rprev = take(nt ? sizeof(float) * Np : 0);
     L.mif = take(nt ? sizeof(int) * MIF_WORDS(kmax) : 0);
     L.dpass = take(sizeof(int));
+    L.spred = take(nt ? sizeof(float) * 3 * Np : 0);
+    L.wsprev = take(sizeof(int));
     L.total = o;
     return L;
 }
@@ -475,6 +477,8 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->ws_loaded = 0;
     c->sms = device_sms();
     c->dpass = (int *)(b + L.dpass);
+    c->spred = (float *)(b + L.spred);
+    c->ws_prev = (int *)(b + L.wsprev);
 
     // zero everything (padding lanes of the SoA arrays included), then draw X_0
     e = cudaMemsetAsync(c->ws, 0, L.total, c->st);
@@ -557,6 +561,8 @@ ssm_status ssm_set_state(ssm_ctx *c, const double *x, int64_t n) {
     if (c->status != SSM_OK) return (ssm_status)c->status;
     cudaError_t e = cudaMemcpyAsync(c->stage, x, sizeof(double) * c->d * c->N, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = launch_aos_to_soa(c->stage, c->x, c->d, c->N, c->Np, c->st);
+    // the learned start's correction refers to the previous step of this run
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws_prev, 0, sizeof(int), c->st);
     if (e == cudaSuccess) e = launch_set_step(c, n);
     if (e == cudaSuccess) e = launch_moments(c);
     // the caller's array may be reused once this returns
@@ -704,6 +710,8 @@ ssm_status ssm_pair_pass(ssm_ctx *c, int which, int64_t *pairs) {
     cudaError_t e;
     if (which == 2) {
         e = ws_forward_start(c);
+        // the start alone leaves predictions that no step converged: no correction next step
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->ws_prev, 0, sizeof(int), c->st);
         if (e != cudaSuccess) { c->status = cuda_status(e); return (ssm_status)c->status; }
         if (pairs) *pairs = 0;
         return SSM_OK;

@@ -166,14 +166,37 @@ __device__ __forceinline__ void cubic_start(const double (&X)[3], const float (&
         for (int c = 0; c < 3; ++c) yi[c * Np] = X[c] + f32_to_f64(dl[c]);
 }
 
+// The prediction used for the start: the network's S_pred, plus -- when the previous
+// step of this run converged from a prediction of this particle -- that step's error
+// S(Y*) - S_pred, kept per particle.  The network sees the particle and the moments
+// of the measure, not the particular sample of N particles; the part of S it cannot
+// predict, the sample's fluctuation about its law (~1/sqrt(N)), is a smooth field
+// that moves little in one step, so the previous error removes most of it (at
+// N = 2^18 the start's error falls from ~6e-7 to ~4e-8, below the ~1e-7 at which one
+// pass and the residual bound suffice).  The raw prediction is kept for the next step.
+__device__ __forceinline__ void corrected_start(const double (&X)[3], const float (&S)[3], double h, double *y,
+                                                const double *__restrict__ sconv, float *__restrict__ spred,
+                                                bool corr, int64_t i, int64_t Np) {
+    float Su[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Su[c] = S[c];
+        if (corr) Su[c] += f64_to_f32_fast(sconv[c * Np + i] - (double)spred[c * Np + i]);
+        spred[c * Np + i] = S[c];
+    }
+    cubic_start(X, Su, h, y + i, Np);
+}
+
 // Learned start of step 1 on the CUDA cores (FFMA, weights broadcast from shared memory).
 __global__ void __launch_bounds__(128)
 k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__restrict__ blob,
-           const double *__restrict__ mom, int64_t N, int64_t Np, double h) {
+           const double *__restrict__ mom, int64_t N, int64_t Np, double h, const double *__restrict__ sconv,
+           float *__restrict__ spred, const int *__restrict__ ws_prev) {
     extern __shared__ float smem[];
     Net &n = *reinterpret_cast<Net *>(smem);
     load_net(blob, n);
     __syncthreads();
+    const bool corr = *ws_prev != 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double X[3];
         float f[NI];
@@ -189,7 +212,7 @@ k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__
         float S[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) S[c] = o[c] * n.ys[c] + n.ym[c];
-        cubic_start(X, S, h, y + i, Np);
+        corrected_start(X, S, h, y, sconv, spred, corr, i, Np);
     }
 }
 
@@ -251,8 +274,10 @@ __device__ __forceinline__ void mma_hidden(const __nv_bfloat16 *W, int ld, const
 
 __global__ void __launch_bounds__(MMA_WARPS * 32)
 k_ws_start_mma(const double *__restrict__ x, double *__restrict__ y, const float *__restrict__ blob,
-               const double *__restrict__ mom, int64_t N, int64_t Np, double h) {
+               const double *__restrict__ mom, int64_t N, int64_t Np, double h, const double *__restrict__ sconv,
+               float *__restrict__ spred, const int *__restrict__ ws_prev) {
     __shared__ MmaNet sm;
+    const bool corr = *ws_prev != 0;
     const __nv_bfloat16 *wg = reinterpret_cast<const __nv_bfloat16 *>(blob + OFF_W);
     for (int k = threadIdx.x; k < NW1; k += blockDim.x) sm.w[(k / NI) * MW_LD1 + k % NI] = wg[k];
     for (int k = threadIdx.x; k < NW2; k += blockDim.x) sm.w[MW_W2 + (k / NH) * MW_LD + k % NH] = wg[NW1 + k];
@@ -322,7 +347,7 @@ k_ws_start_mma(const double *__restrict__ x, double *__restrict__ y, const float
             float S[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) S[c] = out[lane][c] * sm.ys[c] + sm.ym[c];
-            cubic_start(X, S, h, y + i, Np);
+            corrected_start(X, S, h, y, sconv, spred, corr, i, Np);
         }
         __syncwarp();
     }
@@ -541,11 +566,13 @@ cudaError_t ws_forward_start(ssm_ctx *c) {
         if (e != cudaSuccess) return e;
         int64_t blocks = (c->N + 127) / 128;
         if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
-        k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+        k_ws_start<<<(unsigned)blocks, 128, NET_SMEM, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h,
+                                                              c->sconv, c->spred, c->ws_prev);
     } else {
         int64_t blocks = (c->N + MMA_WARPS * 32 - 1) / (MMA_WARPS * 32);
         if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
-        k_ws_start_mma<<<(unsigned)blocks, MMA_WARPS * 32, 0, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np, c->h);
+        k_ws_start_mma<<<(unsigned)blocks, MMA_WARPS * 32, 0, c->st>>>(c->x, c->y, c->ws_w, c->mom, c->N, c->Np,
+                                                                       c->h, c->sconv, c->spred, c->ws_prev);
     }
     return cudaGetLastError();
 }
@@ -622,6 +649,8 @@ ssm_status ssm_ws_load(ssm_ctx *c, const void *blob, size_t bytes) {
     if (!c || !blob_ok(blob, bytes)) return SSM_EINVAL;
     if (c->coef != SSM_COEF_COUPLED3D) return SSM_EINVAL;
     cudaError_t e = cudaMemcpyAsync(c->ws_w, blob, BLOB_BYTES, cudaMemcpyHostToDevice, c->st);
+    // a new network: no previous prediction error to carry over
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws_prev, 0, sizeof(int), c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cst(e);
     c->ws_loaded = 1;
