@@ -221,10 +221,14 @@ k_ws_start(const double *__restrict__ x, double *__restrict__ y, const float *__
 // A warp takes 32 particles at a time and pushes each 16-particle half through the four
 // layers: activations [16 x K] are the A operand, the stored BF16 weights (row-major
 // [out][in], i.e. the B operand in column order) are read from shared memory, the
-// FP32 accumulators get bias and SiLU and are rounded to BF16 pairs that are, register
-// for register, the A operand of the next layer (the m16n8 accumulator layout of two
-// adjacent n-tiles is the m16k16 operand layout).  Rows of W are padded by 8 elements
-// so that the fragment loads of a warp fall in distinct banks.
+// FP32 accumulators get bias and SiLU and become, register for register, the A operand
+// of the next layer (the m16n8 accumulator layout of two adjacent n-tiles is the
+// m16k16 operand layout).  Each activation enters as two BF16 parts, hi = bf16(a) and
+// lo = bf16(a - hi), with two products per tile: the weights are exact in BF16, so
+// the layer is computed to ~2^-16 relative of the activations instead of 2^-8 -- the
+// start carries the previous step's error forward, which cancels only the smooth part
+// of the prediction error, not rounding that jumps from step to step.  Rows of W are
+// padded by 8 elements so that the fragment loads of a warp fall in distinct banks.
 constexpr int MW_LD1 = NI + 8, MW_LD = NH + 8;
 constexpr int MW_W2 = NH * MW_LD1, MW_W3 = MW_W2 + NH * MW_LD, MW_W4 = MW_W3 + NH * MW_LD, MW_TOT = MW_W4 + 8 * MW_LD;
 constexpr int MMA_WARPS = 4;
@@ -232,15 +236,11 @@ struct MmaNet {
     __nv_bfloat16 w[MW_TOT];                          // W1 | W2 | W3 | W4 (8 rows; rows 3..7 zero)
     float b1[NH], b2[NH], b3[NH], b4[8];
     float fm[NI], fsi[NI], ym[4], ys[4];
-    __nv_bfloat16 feat[MMA_WARPS][32][NI + 8];        // a warp's staged, standardised features
+    __nv_bfloat16 feat[MMA_WARPS][2][32][NI + 8];     // a warp's staged, standardised features (hi, lo)
     float out[MMA_WARPS][32][4];                      // a warp's network outputs
 };
 
 __device__ __forceinline__ unsigned lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); }
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const unsigned *>(&v);
-}
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
     asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                  "{%0,%1,%2,%3};"
@@ -249,26 +249,39 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 }
 __device__ __forceinline__ float silu_fast(float s) { return s * rcp_approx(1.0f + ex2_approx(-1.4426950408889634f * s)); }
 
-// One hidden layer: d[j] = A . W^T for the 8 n-tiles of 64 outputs (KT k-tiles of
-// input), then bias + SiLU, repacked in place as the next layer's 4 k-tiles.
+// hi = bf16(v), lo = bf16(v - hi) for a pair of values, packed as two BF16 pairs.
+__device__ __forceinline__ void split_bf16(float v0, float v1, unsigned &hi, unsigned &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+    hi = *reinterpret_cast<const unsigned *>(&h);
+    lo = *reinterpret_cast<const unsigned *>(&l);
+}
+
+// One hidden layer: d[j] = (A_hi + A_lo) . W^T for the 8 n-tiles of 64 outputs (KT
+// k-tiles of input), then bias + SiLU, split and repacked in place as the next
+// layer's 4 k-tiles.
 template <int KT>
-__device__ __forceinline__ void mma_hidden(const __nv_bfloat16 *W, int ld, const float *bias, unsigned (&a)[4][4],
-                                           int g, int t) {
+__device__ __forceinline__ void mma_hidden(const __nv_bfloat16 *W, int ld, const float *bias, unsigned (&ah)[4][4],
+                                           unsigned (&al)[4][4], int g, int t) {
     float d[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.0f;
         const __nv_bfloat16 *row = W + (8 * j + g) * ld + 2 * t;
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) mma_bf16(d[j], a[kk], lds32(row + 16 * kk), lds32(row + 16 * kk + 8));
+        for (int kk = 0; kk < KT; ++kk) {
+            const unsigned b0 = lds32(row + 16 * kk), b1 = lds32(row + 16 * kk + 8);
+            mma_bf16(d[j], al[kk], b0, b1);
+            mma_bf16(d[j], ah[kk], b0, b1);
+        }
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float c0 = bias[8 * j + 2 * t], c1 = bias[8 * j + 2 * t + 1];
-        const unsigned lo = pack_bf16(silu_fast(d[j][0] + c0), silu_fast(d[j][1] + c1));
-        const unsigned hi = pack_bf16(silu_fast(d[j][2] + c0), silu_fast(d[j][3] + c1));
-        a[j >> 1][(j & 1) * 2 + 0] = lo;
-        a[j >> 1][(j & 1) * 2 + 1] = hi;
+        split_bf16(silu_fast(d[j][0] + c0), silu_fast(d[j][1] + c1), ah[j >> 1][(j & 1) * 2 + 0],
+                   al[j >> 1][(j & 1) * 2 + 0]);
+        split_bf16(silu_fast(d[j][2] + c0), silu_fast(d[j][3] + c1), ah[j >> 1][(j & 1) * 2 + 1],
+                   al[j >> 1][(j & 1) * 2 + 1]);
     }
 }
 
@@ -300,7 +313,8 @@ k_ws_start_mma(const double *__restrict__ x, double *__restrict__ y, const float
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16(*feat)[NI + 8] = sm.feat[warp];
+    __nv_bfloat16(*feat)[NI + 8] = sm.feat[warp][0];
+    __nv_bfloat16(*featl)[NI + 8] = sm.feat[warp][1];
     float(*out)[4] = sm.out[warp];
     for (int64_t base = ((int64_t)blockIdx.x * MMA_WARPS + warp) * 32; base < N;
          base += (int64_t)gridDim.x * MMA_WARPS * 32) {
@@ -317,24 +331,32 @@ k_ws_start_mma(const double *__restrict__ x, double *__restrict__ y, const float
         f[15] = (float)h;
 #pragma unroll
         for (int k = 0; k < NI; k += 2)
-            *reinterpret_cast<unsigned *>(&feat[lane][k]) =
-                pack_bf16((f[k] - sm.fm[k]) * sm.fsi[k], (f[k + 1] - sm.fm[k + 1]) * sm.fsi[k + 1]);
+            split_bf16((f[k] - sm.fm[k]) * sm.fsi[k], (f[k + 1] - sm.fm[k + 1]) * sm.fsi[k + 1],
+                       *reinterpret_cast<unsigned *>(&feat[lane][k]), *reinterpret_cast<unsigned *>(&featl[lane][k]));
         __syncwarp();
 #pragma unroll 1
         for (int mt = 0; mt < 2; ++mt) {
             const int r0 = 16 * mt + g, r1 = r0 + 8;
-            unsigned a[4][4];
-            a[0][0] = lds32(&feat[r0][2 * t]);
-            a[0][1] = lds32(&feat[r1][2 * t]);
-            a[0][2] = lds32(&feat[r0][2 * t + 8]);
-            a[0][3] = lds32(&feat[r1][2 * t + 8]);
-            mma_hidden<1>(sm.w, MW_LD1, sm.b1, a, g, t);
-            mma_hidden<4>(sm.w + MW_W2, MW_LD, sm.b2, a, g, t);
-            mma_hidden<4>(sm.w + MW_W3, MW_LD, sm.b3, a, g, t);
+            unsigned ah[4][4], al[4][4];
+            ah[0][0] = lds32(&feat[r0][2 * t]);
+            ah[0][1] = lds32(&feat[r1][2 * t]);
+            ah[0][2] = lds32(&feat[r0][2 * t + 8]);
+            ah[0][3] = lds32(&feat[r1][2 * t + 8]);
+            al[0][0] = lds32(&featl[r0][2 * t]);
+            al[0][1] = lds32(&featl[r1][2 * t]);
+            al[0][2] = lds32(&featl[r0][2 * t + 8]);
+            al[0][3] = lds32(&featl[r1][2 * t + 8]);
+            mma_hidden<1>(sm.w, MW_LD1, sm.b1, ah, al, g, t);
+            mma_hidden<4>(sm.w + MW_W2, MW_LD, sm.b2, ah, al, g, t);
+            mma_hidden<4>(sm.w + MW_W3, MW_LD, sm.b3, ah, al, g, t);
             float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             const __nv_bfloat16 *row = sm.w + MW_W4 + g * MW_LD + 2 * t;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(o, a[kk], lds32(row + 16 * kk), lds32(row + 16 * kk + 8));
+            for (int kk = 0; kk < 4; ++kk) {
+                const unsigned b0 = lds32(row + 16 * kk), b1 = lds32(row + 16 * kk + 8);
+                mma_bf16(o, al[kk], b0, b1);
+                mma_bf16(o, ah[kk], b0, b1);
+            }
             if (t < 2) {   // columns 2t, 2t + 1 of rows r0, r1 (outputs 0..2; column 3 is padding)
                 out[r0][2 * t] = o[0] + sm.b4[2 * t];
                 out[r0][2 * t + 1] = o[1] + sm.b4[2 * t + 1];

@@ -128,14 +128,31 @@ def test_learned_start_keeps_the_roots_and_saves_passes(S, trained):
 
 
 def test_bad_network_falls_back_to_the_plain_start(S):
+    """A network whose prediction is off by 1e6: in the first step every particle
+    misses the tolerance within ws_passes passes and restarts from the plain start;
+    from the second step on the start carries each particle's previous error, which
+    cancels this network's constant offset, so no particle restarts.  Both runs reach
+    the plain form's roots."""
     p = {n: np.zeros(s) for n, s in M.SHAPES}
     p["b4"] = np.array([1e6, -1e6, 1e6])
     blob = M.make_blob(p, np.zeros(16), np.ones(16), np.zeros(3), np.ones(3))
     N, seed, K = 1000, 9, 5
     xp, _ = _run(S, N, seed, K, S.SSM_FP32C)
     xl, sl = _run(S, N, seed, K, S.SSM_FP32C_LEARNED, blob, ws_passes=2)
-    assert sl["fallbacks"] == N * K
+    assert sl["fallbacks"] == N
     assert np.max(np.abs(xl - xp)) < 1e-8
+    # without the carried error (dropped before every step) every step restarts
+    s = S.SSM(d=3, N=N, h=H, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=seed, precision=S.SSM_FP32C_LEARNED,
+              ws_passes=2)
+    s.ws_load(blob)
+    for _ in range(K):
+        s.pair_pass(2)                 # the start alone drops the carried error
+        s.step()
+    st = s.stats()
+    x, _ = s.get_state()
+    s.close()
+    assert st["fallbacks"] == N * K
+    assert np.max(np.abs(x - xp)) < 1e-8
 
 
 def test_learned_form_without_weights_runs_plain(S):
