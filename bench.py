@@ -397,6 +397,46 @@ def aggregate_replicas(torch, world, local_seconds, local_units, device):
     return total, world * local_units / total
 
 
+def time_spread_steps(torch, s, stream, flush, K, M, nvtx=False):
+    """Time K single SSM steps spread evenly over the rest of the run (the learned
+    start's cost depends on the step index: its carried error needs a few steps to
+    settle), with untimed steps in between and an L2 flush before each timed step.
+    Each timed step is bracketed by CUDA events on the context's stream.  Returns the
+    step times (s) and the step-1 passes and pair rows of the timed steps."""
+    x_entry, n_entry = s.get_state()
+    n = n_entry
+    stride = max(1, (M - n) // K)
+    times, passes, rows = [], [], []
+    mid = None
+    for k in range(K):
+        if k == K // 2:
+            mid = s.get_state()            # the state at the middle of the timed sample (untimed)
+        if n + stride > M:                  # more timed steps than the run has left: go back to the entry state
+            s.set_state(x_entry, n_entry)
+            n = n_entry
+        if stride > 1:
+            s.run_steps(stride - 1)         # untimed
+        s.sync()
+        st0 = s.stats()
+        with torch.cuda.stream(stream):
+            flush.zero_()                   # L2 flush (not timed)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        if nvtx:
+            torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select exactly the timed steps
+        ev[0].record(stream)
+        s.run_steps(1)
+        ev[1].record(stream)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
+        ev[1].synchronize()
+        st1 = s.stats()
+        times.append(ev[0].elapsed_time(ev[1]) / 1e3)
+        passes.append(st1["newton_passes"] - st0["newton_passes"])
+        rows.append(st1["newton_rows"] - st0["newton_rows"])
+        n += stride
+    return times, passes, rows, stride, mid
+
+
 def time_kernel(torch, S, s, stream, which, reps):
     """Average duration of one full pair pass (CUDA events on the context's stream)."""
     s.pair_pass(which)   # warm
@@ -455,30 +495,23 @@ def main():
     for _ in range(args.warmup):
         s.run_steps(1)
     s.sync()
-    st0 = s.stats()
+    M_STEPS = int(round(T_END / H))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st0 = s.stats()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
-    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select exactly the timed region
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                       # L2 flush between timed steps (not timed)
-        evs[k][0].record(stream)
-        s.run_steps(1)
-        evs[k][1].record(stream)
+    step_s, step_passes, step_rows, stride, mid_state = time_spread_steps(torch, s, stream, flush, args.steps,
+                                                                          M_STEPS, nvtx=True)
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
     s.sync()
     st1 = s.stats()
-    step_s = [a.elapsed_time(b) / 1e3 for a, b in evs]
     total, value = aggregate_replicas(torch, world, float(sum(step_s)), N_PART * args.steps, dev)
-    newton_passes = (st1["newton_passes"] - st0["newton_passes"]) / args.steps
-    newton_rows = (st1["newton_rows"] - st0["newton_rows"]) / args.steps
+    newton_passes = sum(step_passes) / args.steps
+    newton_rows = sum(step_rows) / args.steps
 
     # dominant kernel in isolation (same stream, CUDA events)
     t_newton = time_kernel(torch, S, s, stream, 0, 3)
@@ -523,17 +556,22 @@ def main():
     except S.SSMError as e:
         roofline["measured_pipes"] = {"error": str(e)}
 
-    # end to end through the C ABI: pinned host state in, step, pinned host state out
+    # end to end through the C ABI, from the middle of the timed sample: every step puts
+    # the state in from pinned host memory, takes the step and reads the new state
+    # back into pinned host memory (each step's output is the next step's input)
     xh = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()
-    xo = torch.empty((N_PART, DIM), dtype=torch.float64, pin_memory=True).numpy()
-    x_cur, n_cur = s.get_state(out=xh)
     e2e_steps = max(1, min(args.steps, 5))
+    x_mid, n_mid = mid_state
+    n_mid = min(n_mid, int(round(T_END / H)) - e2e_steps - 1)
+    s.set_state(x_mid, n_mid)
+    s.run_steps(1)                                     # untimed: the learned start's carried error is rebuilt
+    _, n_e = s.get_state(out=xh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        s.set_state(xh, n_cur)
+        s.set_state(xh, n_e)
         s.run_steps(1)
-        s.get_state(out=xo)
+        _, n_e = s.get_state(out=xh)
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": N_PART * e2e_steps / e2e_dt * world, "unit": "particle-steps/s",
            "h2d_bytes_per_step": N_PART * DIM * 8, "d2h_bytes_per_step": N_PART * DIM * 8,
@@ -602,23 +640,14 @@ def main():
         for w in (0, 1):
             pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
             q.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"])
-        for _ in range(args.warmup):
+        for _ in range(args.warmup + 1):
             q.run_steps(1)
         q.sync()
-        qs0 = q.stats()
-        qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            qev[k][0].record(stream)
-            q.run_steps(1)
-            qev[k][1].record(stream)
-        torch.cuda.synchronize()
-        qt = sum(a.elapsed_time(b) / 1e3 for a, b in qev)
-        qs1 = q.stats()
+        qt_s, _, qrows, _, _ = time_spread_steps(torch, q, stream, flush, args.steps, int(round(T_END / H)))
+        qt = sum(qt_s)
         fp32c_plain = {"value": N_PART * args.steps / qt, "unit": "particle-steps/s",
                        "ms_per_step": 1e3 * qt / args.steps,
-                       "newton_rows_per_step": (qs1["newton_rows"] - qs0["newton_rows"]) / args.steps}
+                       "newton_rows_per_step": sum(qrows) / args.steps}
         q.close()
 
     # plain FP64 GPU SSM on the same workload (comparison of the metric): its own
@@ -690,18 +719,20 @@ def main():
             "config": {"workload": "coupled3d N=2^18 d=3 h=2^-8 T=1 seed=2", "form": form,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (512 MB write, untimed)",
+                       "timed_steps": "%d single steps spread over the run, every %d-th step after %d warm-up steps "
+                                      "(untimed steps in between)" % (args.steps, stride, args.warmup + 1),
                        "newton_passes_per_step": newton_passes, "newton_rows_per_step": newton_rows,
                        "plans": plans},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(round(launches_per_step * args.steps)),
             "fp32c_without_learned_start": fp32c_plain,
-            "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / args.steps,
+            "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / max(1, st1["steps"] - st0["steps"]),
             "plain_fp64": fp64,
             "batched_form": batched,
             "measure_y_form": measure_y,
             "o_n_kernels": o_n,
             "full_run": full_run,
             "learned_start_forward": ws_forward,
-            "floor_accepts_per_step": (st1["floor_accepts"] - st0["floor_accepts"]) / args.steps,
+            "floor_accepts_per_step": (st1["floor_accepts"] - st0["floor_accepts"]) / max(1, st1["steps"] - st0["steps"]),
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -399,8 +399,9 @@ void ssm_batch_destroy(ssm_batch *b);
  * usual passes, where S_start = S_pred plus, from the second step of a run on, the
  * previous step's error S(Y*_i) - S_pred of the same particle (the part of S that
  * the network cannot see -- the fluctuation of the particular sample of N particles
- * about its law -- changes little in one step; ssm_set_state, ssm_ws_load and
- * ssm_pair_pass(ctx, 2) drop the carried error for the next step).  A particle whose residual still exceeds newton_tol after
+ * about its law -- changes little in one step; ssm_ws_load, ssm_pair_pass(ctx, 2)
+ * and ssm_set_state to another step index than the current one drop the carried
+ * error for the next step).  A particle whose residual still exceeds newton_tol after
  * ssm_opts.ws_passes passes restarts from the plain start Y = X (plain Newton is
  * the judge); ssm_stats reports those restarts as fallbacks.
  *

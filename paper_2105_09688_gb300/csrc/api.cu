@@ -155,6 +155,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 
 struct Layout {
     size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, spred, wsprev, total;
+    int64_t part_doubles;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -178,6 +179,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
         part = (size_t)chunks_cap(N, 1);
     }
     L.part = take(sizeof(double) * part * Np);
+    L.part_doubles = (int64_t)part * Np;
     L.mpart = take(sizeof(double) * RED_MAX_BLOCKS * 12);
     L.mom = take(sizeof(double) * 12);
     L.ymean = take(sizeof(double) * 4);
@@ -322,7 +324,7 @@ cudaError_t enqueue_pass_loop(ssm_ctx *c, bool f32) {
     cudaStream_t main_st = c->st;
     c->st = c->st_body;
     cudaError_t eb = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, c->act0, c->cnt, c->N, c->Np, 1.0,
-                               c->part, c->st, c->dpass, (int64_t)(c->act1 - c->act0));
+                               c->part, c->st, c->dpass, (int64_t)(c->act1 - c->act0), c->part_cap);
     if (eb == cudaSuccess) eb = launch_newton_update(c, 0, f32 ? 1 : 0, h);
     c->st = main_st;
     cudaGraph_t captured = nullptr;
@@ -369,7 +371,7 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if (c->opt.fixed_pass_launches) {
             for (int k = 0; k < c->kmax; ++k) {
                 if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, (k & 1) ? c->act1 : c->act0,
-                                   c->cnt + k, c->N, c->Np, 1.0, c->part, c->st)) != cudaSuccess)
+                                   c->cnt + k, c->N, c->Np, 1.0, c->part, c->st, nullptr, 0, c->part_cap)) != cudaSuccess)
                     return e;
                 if ((e = launch_newton_update(c, k, f32 ? 1 : 0, 0)) != cudaSuccess) return e;
             }
@@ -477,6 +479,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->ws_loaded = 0;
     c->sms = device_sms();
     c->dpass = (int *)(b + L.dpass);
+    c->part_cap = L.part_doubles;
     c->spred = (float *)(b + L.spred);
     c->ws_prev = (int *)(b + L.wsprev);
 
@@ -561,8 +564,11 @@ ssm_status ssm_set_state(ssm_ctx *c, const double *x, int64_t n) {
     if (c->status != SSM_OK) return (ssm_status)c->status;
     cudaError_t e = cudaMemcpyAsync(c->stage, x, sizeof(double) * c->d * c->N, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = launch_aos_to_soa(c->stage, c->x, c->d, c->N, c->Np, c->st);
-    // the learned start's correction refers to the previous step of this run
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws_prev, 0, sizeof(int), c->st);
+    // the learned start's carried error refers to the previous step of this run: kept
+    // when the state comes back at the step where it stands (a host round trip of
+    // the current state), dropped otherwise (the start only steers the passes; the
+    // roots are certified to the same tolerance either way)
+    if (e == cudaSuccess && n != c->n) e = cudaMemsetAsync(c->ws_prev, 0, sizeof(int), c->st);
     if (e == cudaSuccess) e = launch_set_step(c, n);
     if (e == cudaSuccess) e = launch_moments(c);
     // the caller's array may be reused once this returns

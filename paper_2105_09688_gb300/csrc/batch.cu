@@ -179,13 +179,13 @@ kb_pair(BEns *ens, int n_ens, const BGlobal *g) {
         const double sc = NEWTON ? 1.0 : E.scale;
         if (E.d == 1) {
             tile_scalar<NEWTON ? PK_NEWTON1 : PK_DRIFT1, T, BT, R1>(src, E.y, act, ntgt, E.Np, j0, j1,
-                                                                     tile * BT * R1, sc, part);
+                                                                     tile * BT * R1, sc, part, E.Np);
         } else if (PK3) {
             tile_packed<NEWTON ? PK_NEWTON3 : PK_DRIFT3, BT, R3, PK3 == 2>(src, E.y, act, ntgt, E.Np, j0, j1,
-                                                                           tile * BT * R3, sc, part);
+                                                                           tile * BT * R3, sc, part, E.Np);
         } else {
             tile_scalar<NEWTON ? PK_NEWTON3 : PK_DRIFT3, T, BT, R3>(src, E.y, act, ntgt, E.Np, j0, j1,
-                                                                     tile * BT * R3, sc, part);
+                                                                     tile * BT * R3, sc, part, E.Np);
         }
     }
 }

@@ -10,6 +10,42 @@
 
 namespace ssm {
 
+// The work of this block: its targets [t0, t0 + tile) of the ntgt targets, its
+// sources [j0, j1), and where its partial sums go (part advanced to its chunk, stride
+// ps).  For a list of active targets (act/cnt, or the pass index in dpass) the
+// launch's blocks are reassigned by dyn_chunks when part_cap > 0: chunk-major over
+// the tiles that hold targets, so the consecutive blocks of a chunk share sources.
+// False when the block has no work (block-uniform).
+template <int TILE, int NC>
+__device__ __forceinline__ bool block_work(const int *&act, const int *&cnt, const int *dpass, int64_t act_stride,
+                                           int64_t N, int64_t Np, int64_t chunk_len, int64_t part_cap, int sub,
+                                           int64_t &ntgt, int64_t &t0, int64_t &j0, int64_t &j1, double *&part,
+                                           int64_t &ps) {
+    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
+    ntgt = act ? (int64_t)(*cnt) : N;
+    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
+    const DynChunks dc = dyn_chunks(ntgt, N, Np, TILE, (int)gridDim.x, (int)gridDim.y, chunk_len, sub, NC,
+                                    act ? part_cap : 0);
+    int64_t tile, chunk;
+    if (dc.tiles == (int)gridDim.x) {
+        tile = blockIdx.x;
+        chunk = blockIdx.y;
+    } else {
+        const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        if (b >= (int64_t)dc.tiles * dc.chunks) return false;
+        chunk = b / dc.tiles;
+        tile = b - chunk * dc.tiles;
+    }
+    t0 = tile * TILE;
+    if (t0 >= ntgt) return false;
+    j0 = chunk * dc.len;
+    j1 = (j0 + dc.len < N) ? j0 + dc.len : N;
+    if (j0 >= j1) return false;
+    ps = dc.stride;
+    part += chunk * NC * ps;
+    return true;
+}
+
 // act/cnt: optional compacted target list (targets t < *cnt are particles act[t]).
 // dpass (optional): the pass index of step 1 in device memory, for launches inside a
 // device-driven pass loop; then the list is act + (pass & 1) act_stride (the two
@@ -18,32 +54,28 @@ template <int KIND, typename T, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS)
 k_pair(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
        const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-       double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
-    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    int64_t ntgt = act ? (int64_t)(*cnt) : N;
-    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
-    const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
-    if (t0 >= ntgt) return;   // block-uniform
-    const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
-    const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
-    tile_scalar<KIND, T, THREADS, R>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
-                                     part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
+       double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride, int64_t part_cap) {
+    int64_t ntgt, t0, j0, j1, ps;
+    const int *a = act, *cn = cnt;
+    double *pt = part;
+    if (!block_work<THREADS * R, KindInfo<KIND>::NC>(a, cn, dpass, act_stride, N, Np, chunk_len, part_cap,
+                                                      pair_sub(KIND, 0), ntgt, t0, j0, j1, pt, ps))
+        return;   // block-uniform
+    tile_scalar<KIND, T, THREADS, R>(src, tgt, a, ntgt, Np, j0, j1, t0, scale, pt, ps);
 }
 
 template <int KIND, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS)
 k_pair2(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
         const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-        double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
-    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    int64_t ntgt = act ? (int64_t)(*cnt) : N;
-    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
-    const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
-    if (t0 >= ntgt) return;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
-    const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
-    tile_packed<KIND, THREADS, R, false>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
-                                         part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
+        double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride, int64_t part_cap) {
+    int64_t ntgt, t0, j0, j1, ps;
+    const int *a = act, *cn = cnt;
+    double *pt = part;
+    if (!block_work<THREADS * R, KindInfo<KIND>::NC>(a, cn, dpass, act_stride, N, Np, chunk_len, part_cap,
+                                                      pair_sub(KIND, 1), ntgt, t0, j0, j1, pt, ps))
+        return;
+    tile_packed<KIND, THREADS, R, false>(src, tgt, a, ntgt, Np, j0, j1, t0, scale, pt, ps);
 }
 
 // Centred expansion where a block's targets allow it (difference form otherwise).
@@ -51,40 +83,38 @@ template <int KIND, int THREADS, int R>
 __global__ void __launch_bounds__(THREADS, packed_min_blocks(THREADS, R))
 k_pair2x(const double *__restrict__ src, const double *__restrict__ tgt, const int *__restrict__ act,
          const int *__restrict__ cnt, int64_t N, int64_t Np, int64_t chunk_len, double scale,
-         double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride) {
-    if (dpass) { const int pass = *dpass; act += (pass & 1) * act_stride; cnt += pass; }
-    int64_t ntgt = act ? (int64_t)(*cnt) : N;
-    if (!SSM_IN_BOUNDS(ntgt >= 0 && ntgt <= Np)) ntgt = 0;
-    const int64_t t0 = (int64_t)blockIdx.x * (THREADS * R);
-    if (t0 >= ntgt) return;
-    const int64_t j0 = (int64_t)blockIdx.y * chunk_len;
-    const int64_t j1 = (j0 + chunk_len < N) ? j0 + chunk_len : N;
-    tile_packed<KIND, THREADS, R, true>(src, tgt, act, ntgt, Np, j0, j1, t0, scale,
-                                        part + (int64_t)blockIdx.y * KindInfo<KIND>::NC * Np);
+         double *__restrict__ part, const int *__restrict__ dpass, int64_t act_stride, int64_t part_cap) {
+    int64_t ntgt, t0, j0, j1, ps;
+    const int *a = act, *cn = cnt;
+    double *pt = part;
+    if (!block_work<THREADS * R, KindInfo<KIND>::NC>(a, cn, dpass, act_stride, N, Np, chunk_len, part_cap,
+                                                      pair_sub(KIND, 1), ntgt, t0, j0, j1, pt, ps))
+        return;
+    tile_packed<KIND, THREADS, R, true>(src, tgt, a, ntgt, Np, j0, j1, t0, scale, pt, ps);
 }
 
 template <int KIND, typename T, int THREADS, int R>
 static cudaError_t launch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
                           int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
-                          int64_t act_stride) {
+                          int64_t act_stride, int64_t part_cap) {
     const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)p.chunks);
     k_pair<KIND, T, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part, dpass,
-                                                          act_stride);
+                                                          act_stride, part_cap);
     return cudaGetLastError();
 }
 template <int KIND, int THREADS, int R>
 static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
                            int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
-                           int64_t act_stride) {
+                           int64_t act_stride, int64_t part_cap) {
     const int64_t tiles = (N + THREADS * R - 1) / (THREADS * R);
     dim3 grid((unsigned)tiles, (unsigned)p.chunks);
     if (p.vec2 == 2)
         k_pair2x<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part,
-                                                             dpass, act_stride);
+                                                             dpass, act_stride, part_cap);
     else
         k_pair2<KIND, THREADS, R><<<grid, THREADS, 0, st>>>(src, tgt, act, cnt, N, Np, p.chunk_len, scale, part,
-                                                            dpass, act_stride);
+                                                            dpass, act_stride, part_cap);
     return cudaGetLastError();
 }
 
@@ -96,10 +126,10 @@ static cudaError_t launch2(const Plan &p, const double *src, const double *tgt, 
 template <int KIND, typename T>
 static cudaError_t dispatch(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
                             int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
-                            int64_t act_stride) {
+                            int64_t act_stride, int64_t part_cap) {
 #define SSM_CASE(TH, RR) \
     if (p.threads == TH && p.rpt == RR) \
-        return launch<KIND, T, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+        return launch<KIND, T, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap);
     SSM_PAIR_SHAPES(SSM_CASE)
 #undef SSM_CASE
     return cudaErrorInvalidValue;
@@ -107,10 +137,10 @@ static cudaError_t dispatch(const Plan &p, const double *src, const double *tgt,
 template <int KIND>
 static cudaError_t dispatch2(const Plan &p, const double *src, const double *tgt, const int *act, const int *cnt,
                              int64_t N, int64_t Np, double scale, double *part, cudaStream_t st, const int *dpass,
-                             int64_t act_stride) {
+                             int64_t act_stride, int64_t part_cap) {
 #define SSM_CASE(TH, RR) \
     if (p.threads == TH && p.rpt == RR) \
-        return launch2<KIND, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+        return launch2<KIND, TH, RR>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap);
     SSM_PAIR2_SHAPES(SSM_CASE)
 #undef SSM_CASE
     return cudaErrorInvalidValue;
@@ -118,17 +148,17 @@ static cudaError_t dispatch2(const Plan &p, const double *src, const double *tgt
 
 cudaError_t pair_sums(int kind, bool fp32, const Plan &p, const double *src, const double *tgt, const int *act,
                       const int *cnt, int64_t N, int64_t Np, double scale, double *part, cudaStream_t st,
-                      const int *dpass, int64_t act_stride) {
+                      const int *dpass, int64_t act_stride, int64_t part_cap) {
     if (fp32 && p.vec2) {
         if (kind == PK_NEWTON3)
-            return dispatch2<PK_NEWTON3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+            return dispatch2<PK_NEWTON3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap);
         if (kind == PK_DRIFT3)
-            return dispatch2<PK_DRIFT3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+            return dispatch2<PK_DRIFT3>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap);
         return cudaErrorInvalidValue;
     }
 #define SSM_KIND(K) \
-    case K: return fp32 ? dispatch<K, float>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride) \
-                        : dispatch<K, double>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride);
+    case K: return fp32 ? dispatch<K, float>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap) \
+                        : dispatch<K, double>(p, src, tgt, act, cnt, N, Np, scale, part, st, dpass, act_stride, part_cap);
     switch (kind) {
         SSM_KIND(PK_DRIFT1)
         SSM_KIND(PK_DRIFT3)

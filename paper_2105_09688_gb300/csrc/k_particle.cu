@@ -338,8 +338,8 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
 template <int D, bool LOOP>
 __global__ void __launch_bounds__(256)
 k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act0,
-                int *__restrict__ act1, int *__restrict__ cnt, const double *__restrict__ part, int chunks,
-                int64_t N, int64_t Np, double h, double tol, int fp32_targets, int pass_arg, int kmax,
+                int *__restrict__ act1, int *__restrict__ cnt, const double *__restrict__ part, Plan plan, int sub,
+                int64_t part_cap, int64_t N, int64_t Np, double h, double tol, int fp32_targets, int pass_arg, int kmax,
                 int *__restrict__ passes, long long *hist, int *err, double *__restrict__ sconv, int restart_pass,
                 long long *counters, float *__restrict__ rprev, int *__restrict__ dpass, unsigned *ticket,
                 cudaGraphConditionalHandle hpass) {
@@ -358,6 +358,10 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__res
     int64_t n_in = *cnt_in;
     if (t == 0 && !SSM_IN_BOUNDS(n_in >= 0 && n_in <= N)) n_in = 0;
     if (!(n_in >= 0 && n_in <= N)) n_in = 0;
+    // the chunking the pair kernel used for this many targets
+    const int tile = plan.threads * plan.rpt;
+    const DynChunks dc = dyn_chunks(n_in, N, Np, tile, (int)((N + tile - 1) / tile), plan.chunks, plan.chunk_len, sub,
+                                    NC, part_cap);
     bool keep = false;
     int i = 0;
     if (t < n_in && SSM_IN_BOUNDS(act_in[t] >= 0 && act_in[t] < N)) {
@@ -365,11 +369,11 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__res
         double S[D], Sw = 0.0, Y[D], X[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) S[c] = 0.0;
-        for (int k = 0; k < chunks; ++k) {
-            const double *pk = part + (int64_t)k * NC * Np + t;
+        for (int k = 0; k < dc.chunks; ++k) {
+            const double *pk = part + (int64_t)k * NC * dc.stride + t;
 #pragma unroll
-            for (int c = 0; c < D; ++c) S[c] += pk[c * Np];
-            Sw += pk[D * Np];
+            for (int c = 0; c < D; ++c) S[c] += pk[c * dc.stride];
+            Sw += pk[D * dc.stride];
         }
         const double invN = 1.0 / (double)N;
 #pragma unroll
@@ -843,11 +847,13 @@ cudaError_t launch_newton_begin(ssm_ctx *c) {
 
 // Update of pass `pass` (hpass == 0), or of the pass *c->dpass inside the step
 // graph's device-driven loop whose condition is hpass.
+#define D_KIND(d) ((d) == 1 ? PK_NEWTON1 : PK_NEWTON3)
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, int fp32, cudaGraphConditionalHandle hpass) {
     const int rp = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1;
+    const int sub = pair_sub(D_KIND(c->d), c->plan_newton.vec2);
 #define SSM_UPD1(D, L) k_newton_update<D, L><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->act1, \
-        c->cnt, c->part, c->plan_newton.chunks, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, c->passes, c->hist, \
-        c->err, c->sconv, rp, c->counters, c->rprev, c->dpass, c->ticket, hpass)
+        c->cnt, c->part, c->plan_newton, sub, c->part_cap, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, \
+        c->passes, c->hist, c->err, c->sconv, rp, c->counters, c->rprev, c->dpass, c->ticket, hpass)
 #define SSM_UPD(D) { if (hpass) SSM_UPD1(D, true); else SSM_UPD1(D, false); }
     if (c->d == 1) SSM_UPD(1)
     else SSM_UPD(3)

@@ -13,7 +13,8 @@
 //
 // (y' = scale * y turns the Gaussian kernels exp(-c r^2) of the drift into base-2
 // exponentials; the FP64 forms use exp directly).  The results go to
-// part[c * Np + t] for target slot t (the caller offsets part by chunk).
+// part[c * ps + t] for target slot t (the caller offsets part by chunk; ps is the
+// stride of the partial sums, Np unless a pass over few targets packs them).
 //
 // A pairwise nonlinear kernel is not a contraction, so it runs on the FP32 (or
 // FP64) CUDA-core pipes: each thread holds R targets in registers; sources are
@@ -139,7 +140,8 @@ template <> __device__ __forceinline__ double cvt<double>(double v, double scale
 template <int KIND, typename T, int THREADS, int R>
 __device__ __forceinline__ void tile_scalar(const double *__restrict__ src, const double *__restrict__ tgt,
                                             const int *__restrict__ act, int64_t ntgt, int64_t Np, int64_t j0,
-                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part) {
+                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part,
+                                            int64_t ps) {
     constexpr int D = KindInfo<KIND>::D, NC = KindInfo<KIND>::NC;
     using V = typename V4<T>::t;
     __shared__ V sm[SUB];
@@ -210,7 +212,7 @@ __device__ __forceinline__ void tile_scalar(const double *__restrict__ src, cons
         if (t < ntgt) {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                part[(int64_t)c * Np + t] = sizeof(T) == 4 ? (double)hi[r][c] + (double)lo[r][c] : (double)acc[r][c];
+                part[(int64_t)c * ps + t] = sizeof(T) == 4 ? (double)hi[r][c] + (double)lo[r][c] : (double)acc[r][c];
         }
     }
 }
@@ -376,7 +378,7 @@ template <int KIND, int THREADS, int R>
 __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                  const double *__restrict__ tgt, const int *__restrict__ act,
                                                  int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
-                                                 double scale, double *__restrict__ part) {
+                                                 double scale, double *__restrict__ part, int64_t ps) {
     constexpr int NC = PackedInfo<KIND>::NC, R2 = R / 2, SUBP = PackedInfo<KIND>::SUBP;
     float4 *sxy = buf;                              // (x, x, y, y)
     float2 *szz = reinterpret_cast<float2 *>(buf + SUBP);   // (z, z)
@@ -442,7 +444,7 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const f
             const int64_t t = t0 + (2 * k + e) * THREADS + tid;
             if (t < ntgt) {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) part[(int64_t)c * Np + t] = comp.value(k, c, e);
+                for (int c = 0; c < NC; ++c) part[(int64_t)c * ps + t] = comp.value(k, c, e);
             }
         }
 }
@@ -457,7 +459,8 @@ template <int KIND, int THREADS, int R>
 __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                 const double *__restrict__ tgt, const int *__restrict__ act,
                                                 int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
-                                                double scale, const double (&cc)[3], double *__restrict__ part) {
+                                                double scale, const double (&cc)[3], double *__restrict__ part,
+                                                int64_t ps) {
     constexpr bool NEWTON = KIND == PK_NEWTON3;
     constexpr int NX = PackedInfo<KIND>::NX, R2 = R / 2, SUBP = PackedInfo<KIND>::SUBP;
     const int tid = threadIdx.x;
@@ -539,9 +542,9 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const double yc = tgt[c * Np + i];
-                        part[(int64_t)c * Np + t] = S[c] - ((double)(float)yc - cc[c]) * S[3];
+                        part[(int64_t)c * ps + t] = S[c] - ((double)(float)yc - cc[c]) * S[3];
                     }
-                    part[(int64_t)3 * Np + t] = S[3];
+                    part[(int64_t)3 * ps + t] = S[3];
                 } else {
                     const float2 tu[3] = {ux[k], uy[k], uz[k]};
                     double b2 = 0.0;
@@ -553,7 +556,7 @@ __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const fl
                     const double f = exp2(-b2);
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        part[(int64_t)c * Np + t] = f * (S[c] - (tgt[c * Np + i] - cc[c]) * scale * S[3]);
+                        part[(int64_t)c * ps + t] = f * (S[c] - (tgt[c * Np + i] - cc[c]) * scale * S[3]);
                 }
             }
         }
@@ -572,7 +575,8 @@ __host__ __device__ constexpr int packed_min_blocks(int threads, int r) {
 template <int KIND, int THREADS, int R, bool EXPAND>
 __device__ __forceinline__ void tile_packed(const double *__restrict__ src, const double *__restrict__ tgt,
                                             const int *__restrict__ act, int64_t ntgt, int64_t Np, int64_t j0,
-                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part) {
+                                            int64_t j1, int64_t t0, double scale, double *__restrict__ part,
+                                            int64_t ps) {
     static_assert(R % 2 == 0, "targets per thread come in pairs");
     static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
     __shared__ float4 buf[2 * PackedInfo<KIND>::SUBP];
@@ -623,11 +627,12 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
             }
         }
         if (__syncthreads_and(ok)) {
-            tile_packed_exp<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part);
+            tile_packed_exp<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part,
+                                              ps);
             return;
         }
     }
-    tile_packed_diff<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, part);
+    tile_packed_diff<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, part, ps);
 }
 
 }  // namespace ssm

@@ -42,6 +42,18 @@ def _child():
             else:
                 assert err < 2e-6, (N, err)
             worst = max(worst, err)
+    # several target tiles: passes over part of the particles repack the pair kernel's
+    # blocks and partial sums (the partial-pass chunking), here under the index checks
+    for N in (3000, 5000):
+        s = S.SSM(d=3, N=N, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=6, precision=S.SSM_FP32C)
+        s.run_steps(3)
+        x, _ = s.get_state()
+        st = s.stats()
+        s.close()
+        P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=2.0 ** -8, seed=6)
+        xo = O.run(P, O.init_x0(P), 0, 3)
+        assert np.max(np.abs(x - xo)) < 2e-6
+        assert st["newton_rows"] < st["newton_passes"] * N     # some passes were partial
     s = S.SSM(d=1, N=7, h=0.01, T=1.0, coef=S.SSM_COEF_CUBIC1D_GAUSS, seed=0)
     s.run_steps(3)
     s.sync()
