@@ -41,17 +41,24 @@ FLOPS_PAIR_WITH_WSUM = 16.0              # step-1 count including the weight sum
 # operations): step 1: 1 + 3 x 2 (q) + 3 x 2 + 1 = 14; drift: 3 x 2 + 3 x 2 + 1 = 13.
 FLOPS_PAIR_EXPANDED = {0: 14.0, 1: 13.0}
 FORM_NAMES = {0: "scalar", 1: "packed difference form", 2: "packed centred expansion"}
-# DRAM bytes (read + write) of one step-1 pair launch, k_pair2x<PK_NEWTON3, 128, 4> at
-# N = 2^18, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), for
-# each source-chunk count the autotuner can pick for that shape (the partial sums
-# written grow with it); valid only for the kernel sources they were measured on
-# (the tile code and its launchers, SHA-256 below), otherwise the roofline's traffic
-# is null.
-MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 128, 4, 1 << 18),
-                    "bytes_by_chunks": {13: 13088000 + 48971008, 19: 15219968 + 100673536,
-                                        26: 16034304 + 159384576, 32: 15156480 + 209587968},
+# DRAM bytes (read + write) of one step-1 pair launch of the centred-expansion kernel
+# k_pair2x<PK_NEWTON3, threads, rpt> at N = 2^18, from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (threads, targets per
+# thread, source chunks) for the shapes and chunk counts the autotuner picks among
+# (the partial sums written grow with the chunks); valid only for the kernel sources
+# they were measured on (the tile code and its launchers, SHA-256 below), otherwise
+# the roofline's traffic is null.
+MEASURED_TRAFFIC = {"kernel": ("k_pair2x", 0, 1 << 18),
+                    "bytes": {(128, 4, 13): 14148096 + 50406656,
+                              (128, 4, 19): 13293568 + 99668480,
+                              (128, 4, 26): 16857600 + 159375104,
+                              (128, 4, 32): 16656128 + 209221888,
+                              (128, 8, 7): 13107456 + 2366464,
+                              (128, 8, 10): 13922816 + 25005312,
+                              (128, 8, 14): 13753344 + 57894144,
+                              (128, 8, 17): 14568192 + 82809088},
                     "sources": ("paper_2105_09688_gb300/csrc/pair_tile.cuh", "paper_2105_09688_gb300/csrc/k_pair.cu"),
-                    "sha256": "212ba0fddeb4208920fb05eb4488f1a560fb4d88749b4513c610cc826b9fbe73"}
+                    "sha256": "c9553bd4d11365f463499e3a028266f900b5a19d59551615d0fe122f59e8e401"}
 
 
 def measured_traffic(kernel, kind, threads, rpt, n, chunks):
@@ -59,13 +66,13 @@ def measured_traffic(kernel, kind, threads, rpt, n, chunks):
     current sources, else None."""
     import hashlib
     m = MEASURED_TRAFFIC
-    if (kernel, kind, threads, rpt, n) != m["kernel"] or chunks not in m["bytes_by_chunks"]:
+    if (kernel, kind, n) != m["kernel"] or (threads, rpt, chunks) not in m["bytes"]:
         return None
     h = hashlib.sha256()
     for f in m["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return m["bytes_by_chunks"][chunks] if h.hexdigest() == m["sha256"] else None
+    return m["bytes"][(threads, rpt, chunks)] if h.hexdigest() == m["sha256"] else None
 METRIC = "particle-steps/s, N=2^18 d=3: learned+FP32 vs plain FP64 SSM at stated error"
 
 

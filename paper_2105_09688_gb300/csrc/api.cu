@@ -154,7 +154,7 @@ Plan make_plan(int64_t N, bool fp32, int kind, int force_chunks) {
 }
 
 struct Layout {
-    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, spred, wsprev, total;
+    size_t x, y, stage, part, mpart, mom, ymean, act0, act1, cnt, passes, err, ticket, dstep, counters, hist, wsw, sconv, mom_prev, rprev, mif, dpass, pplan, spred, wsprev, total;
     int64_t part_doubles;
 };
 
@@ -199,6 +199,7 @@ Layout make_layout(int d, int64_t N, int coef, int kmax) {
     L.rprev = take(nt ? sizeof(float) * Np : 0);
     L.mif = take(nt ? sizeof(int) * MIF_WORDS(kmax) : 0);
     L.dpass = take(sizeof(int));
+    L.pplan = take(sizeof(DynChunks));
     L.spred = take(nt ? sizeof(float) * 3 * Np : 0);
     L.wsprev = take(sizeof(int));
     L.total = o;
@@ -324,7 +325,7 @@ cudaError_t enqueue_pass_loop(ssm_ctx *c, bool f32) {
     cudaStream_t main_st = c->st;
     c->st = c->st_body;
     cudaError_t eb = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, c->act0, c->cnt, c->N, c->Np, 1.0,
-                               c->part, c->st, c->dpass, (int64_t)(c->act1 - c->act0), c->part_cap);
+                               c->part, c->st, c->dpass, (int64_t)(c->act1 - c->act0), c->pplan);
     if (eb == cudaSuccess) eb = launch_newton_update(c, 0, f32 ? 1 : 0, h);
     c->st = main_st;
     cudaGraph_t captured = nullptr;
@@ -371,7 +372,7 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if (c->opt.fixed_pass_launches) {
             for (int k = 0; k < c->kmax; ++k) {
                 if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, (k & 1) ? c->act1 : c->act0,
-                                   c->cnt + k, c->N, c->Np, 1.0, c->part, c->st, nullptr, 0, c->part_cap)) != cudaSuccess)
+                                   c->cnt + k, c->N, c->Np, 1.0, c->part, c->st, nullptr, 0, c->pplan)) != cudaSuccess)
                     return e;
                 if ((e = launch_newton_update(c, k, f32 ? 1 : 0, 0)) != cudaSuccess) return e;
             }
@@ -480,6 +481,7 @@ ssm_status ssm_create(int d, int64_t N, double h, double T, int coef, uint64_t s
     c->sms = device_sms();
     c->dpass = (int *)(b + L.dpass);
     c->part_cap = L.part_doubles;
+    c->pplan = (DynChunks *)(b + L.pplan);
     c->spred = (float *)(b + L.spred);
     c->ws_prev = (int *)(b + L.wsprev);
 

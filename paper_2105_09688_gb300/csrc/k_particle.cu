@@ -305,7 +305,7 @@ template <int D>
 __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act,
                                int *__restrict__ cnt, int kmax, int *__restrict__ passes, long long *hist,
                                const double *__restrict__ mom, double *__restrict__ mom_prev, int64_t N, int64_t Np,
-                               int *__restrict__ dpass, int inject) {
+                               int *__restrict__ dpass, int inject, DynChunks *pplan, DynChunks full) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
 #pragma unroll
@@ -319,6 +319,7 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
         for (int k = 0; k < 16; ++k) hist[k] = 0;
         for (int k = 0; k < 4 * D; ++k) mom_prev[k] = mom[k];
         *dpass = 0;
+        *pplan = full;   // the first pass covers every particle: the planned shape
 #ifdef SSM_CHECK_BOUNDS
         // ssm_opts.inject = 1 (debug builds, N not a multiple of 128): list entry 0
         // names particle N, past the particles but inside the padded arrays, for
@@ -338,8 +339,9 @@ __global__ void k_newton_begin(const double *__restrict__ x, double *__restrict_
 template <int D, bool LOOP>
 __global__ void __launch_bounds__(256)
 k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__restrict__ act0,
-                int *__restrict__ act1, int *__restrict__ cnt, const double *__restrict__ part, Plan plan, int sub,
-                int64_t part_cap, int64_t N, int64_t Np, double h, double tol, int fp32_targets, int pass_arg, int kmax,
+                int *__restrict__ act1, int *__restrict__ cnt, const double *__restrict__ part, DynChunks *pplan,
+                Plan plan, int sub, int64_t part_cap, int64_t N, int64_t Np, double h, double tol, int fp32_targets,
+                int pass_arg, int kmax,
                 int *__restrict__ passes, long long *hist, int *err, double *__restrict__ sconv, int restart_pass,
                 long long *counters, float *__restrict__ rprev, int *__restrict__ dpass, unsigned *ticket,
                 cudaGraphConditionalHandle hpass) {
@@ -358,10 +360,7 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__res
     int64_t n_in = *cnt_in;
     if (t == 0 && !SSM_IN_BOUNDS(n_in >= 0 && n_in <= N)) n_in = 0;
     if (!(n_in >= 0 && n_in <= N)) n_in = 0;
-    // the chunking the pair kernel used for this many targets
-    const int tile = plan.threads * plan.rpt;
-    const DynChunks dc = dyn_chunks(n_in, N, Np, tile, (int)((N + tile - 1) / tile), plan.chunks, plan.chunk_len, sub,
-                                    NC, part_cap);
+    const DynChunks dc = *pplan;   // the chunking the pair kernel used for this pass
     bool keep = false;
     int i = 0;
     if (t < n_in && SSM_IN_BOUNDS(act_in[t] >= 0 && act_in[t] < N)) {
@@ -421,9 +420,15 @@ k_newton_update(const double *__restrict__ x, double *__restrict__ y, int *__res
         atomicAdd((unsigned long long *)&counters[CNT_FALLBACKS], (unsigned long long)nrestart);
     if (threadIdx.x == 0 && nfloor)
         atomicAdd((unsigned long long *)&counters[CNT_FLOOR], (unsigned long long)nfloor);
-    if constexpr (LOOP) {
-        if (last_block(ticket) && threadIdx.x == 0) {
-            const int next = __ldcg(cnt_out);   // every block's appends are complete and visible
+    // the last block (every block has read this pass's plan and appended its survivors)
+    // writes the chunking of the next pass and, in the device-driven loop, its index
+    // and whether it runs
+    if (last_block(ticket) && threadIdx.x == 0) {
+        const int next = __ldcg(cnt_out);
+        const int tile = plan.threads * plan.rpt;
+        *pplan = dyn_chunks(next, N, Np, tile, (int)((N + tile - 1) / tile), plan.chunks, plan.chunk_len, sub, NC,
+                            part_cap);
+        if constexpr (LOOP) {
             *dpass = pass + 1;
             cudaGraphSetConditional(hpass, (next > 0 && pass + 1 < kmax) ? 1u : 0u);
         }
@@ -833,26 +838,30 @@ cudaError_t launch_mm_implicit(ssm_ctx *c) {
     return cudaGetLastError();
 }
 
+#define D_KIND(d) ((d) == 1 ? PK_NEWTON1 : PK_NEWTON3)
 cudaError_t launch_newton_begin(ssm_ctx *c) {
+    const int tile = c->plan_newton.threads * c->plan_newton.rpt;
+    const DynChunks full = dyn_chunks(c->N, c->N, c->Np, tile, (int)((c->N + tile - 1) / tile), c->plan_newton.chunks,
+                                      c->plan_newton.chunk_len, pair_sub(D_KIND(c->d), c->plan_newton.vec2), c->d + 1,
+                                      c->part_cap);
     if (c->d == 1)
         k_newton_begin<1><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
                                                               c->mom, c->mom_prev, c->N, c->Np, c->dpass,
-                                                              c->opt.inject);
+                                                              c->opt.inject, c->pplan, full);
     else
         k_newton_begin<3><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->cnt, c->kmax, c->passes, c->hist,
                                                               c->mom, c->mom_prev, c->N, c->Np, c->dpass,
-                                                              c->opt.inject);
+                                                              c->opt.inject, c->pplan, full);
     return cudaGetLastError();
 }
 
 // Update of pass `pass` (hpass == 0), or of the pass *c->dpass inside the step
 // graph's device-driven loop whose condition is hpass.
-#define D_KIND(d) ((d) == 1 ? PK_NEWTON1 : PK_NEWTON3)
 cudaError_t launch_newton_update(ssm_ctx *c, int pass, int fp32, cudaGraphConditionalHandle hpass) {
     const int rp = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded) ? c->opt.ws_passes : -1;
     const int sub = pair_sub(D_KIND(c->d), c->plan_newton.vec2);
 #define SSM_UPD1(D, L) k_newton_update<D, L><<<nblk(c->N, 256), 256, 0, c->st>>>(c->x, c->y, c->act0, c->act1, \
-        c->cnt, c->part, c->plan_newton, sub, c->part_cap, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, \
+        c->cnt, c->part, c->pplan, c->plan_newton, sub, c->part_cap, c->N, c->Np, c->h, c->tol, fp32, pass, c->kmax, \
         c->passes, c->hist, c->err, c->sconv, rp, c->counters, c->rprev, c->dpass, c->ticket, hpass)
 #define SSM_UPD(D) { if (hpass) SSM_UPD1(D, true); else SSM_UPD1(D, false); }
     if (c->d == 1) SSM_UPD(1)

@@ -13,8 +13,8 @@
 //
 // (y' = scale * y turns the Gaussian kernels exp(-c r^2) of the drift into base-2
 // exponentials; the FP64 forms use exp directly).  The results go to
-// part[c * ps + t] for target slot t (the caller offsets part by chunk; ps is the
-// stride of the partial sums, Np unless a pass over few targets packs them).
+// part[c * ps + t] for target slot t (the caller offsets part by chunk and gives
+// the stride ps of the partial sums).
 //
 // A pairwise nonlinear kernel is not a contraction, so it runs on the FP32 (or
 // FP64) CUDA-core pipes: each thread holds R targets in registers; sources are
@@ -455,11 +455,11 @@ __device__ __forceinline__ void tile_packed_diff(float4 *buf, float *hl, const f
 //           consumer's correction of the FP32 target, -(y - fl(y)) sum w, still
 //           applies (the linear t_i term is taken in FP64 here);
 //   drift : sum_j e_ij (s_j - t_i) in scaled units, t_i = scale (y_i - c) exact.
-template <int KIND, int THREADS, int R>
+template <int KIND, int THREADS, int R, typename CC>
 __device__ __forceinline__ void tile_packed_exp(float4 *buf, float *hl, const float2 *s_one, const double *__restrict__ src,
                                                 const double *__restrict__ tgt, const int *__restrict__ act,
                                                 int64_t ntgt, int64_t Np, int64_t j0, int64_t j1, int64_t t0,
-                                                double scale, const double (&cc)[3], double *__restrict__ part,
+                                                double scale, const CC &cc, double *__restrict__ part,
                                                 int64_t ps) {
     constexpr bool NEWTON = KIND == PK_NEWTON3;
     constexpr int NX = PackedInfo<KIND>::NX, R2 = R / 2, SUBP = PackedInfo<KIND>::SUBP;
@@ -626,7 +626,17 @@ __device__ __forceinline__ void tile_packed(const double *__restrict__ src, cons
                 ok &= (a * a + b * b + d * d <= (double)EXP_R2) ? 1 : 0;   // false for NaN
             }
         }
-        if (__syncthreads_and(ok)) {
+        // The step-1 kind reads the centre from shared memory in its loop and the
+        // drift kind from registers: the register allocations that time fastest.
+        if constexpr (KIND == PK_NEWTON3) {
+            __shared__ double s_cc[3];
+            if (tid < 3) s_cc[tid] = cc[tid];
+            if (__syncthreads_and(ok)) {
+                tile_packed_exp<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, s_cc,
+                                                  part, ps);
+                return;
+            }
+        } else if (__syncthreads_and(ok)) {
             tile_packed_exp<KIND, THREADS, R>(buf, s_hl, &s_one, src, tgt, act, ntgt, Np, j0, j1, t0, scale, cc, part,
                                               ps);
             return;
