@@ -302,7 +302,18 @@ MOMENT_MODELS = {"gl1": (1, "SSM_COEF_GL1", (1.5, 0.5), 1.0, 0.0),
                  "gl2": (1, "SSM_COEF_GL2", (1.5, 0.5), 1.0, 0.0),
                  "poly": (1, "SSM_COEF_POLY", (-1.0,), 1.0, 0.0),
                  "cs": (2, "SSM_COEF_CS", (2.0, 4.0), 1.0, 2.0 ** 0.5)}
-ON_BYTES_PER_PARTICLE_STEP = 4 * 8 * ON_D   # implicit step: read X, write Y; step 2: read Y, write X (FP64)
+# Algorithmic FP64 bytes per particle-step and component of the O(N) step.  OU and
+# the polynomial drift take step 1 inside step 2's kernel (X read, the stage Y and
+# the new X written: 3 x 8 bytes); the cubic sets run step 1 as its own kernel (X
+# read, Y written; then Y read, X written: 4 x 8 bytes).
+FUSED_STEP1 = ("SSM_COEF_OU", "SSM_COEF_POLY")
+
+
+def o_n_bytes(cname, d):
+    return (3 if cname in FUSED_STEP1 else 4) * 8 * d
+
+
+ON_BYTES_PER_PARTICLE_STEP = o_n_bytes("SSM_COEF_OU", ON_D)
 
 
 def measured_peaks():
@@ -344,14 +355,14 @@ def hbm_peak_gbs():
 
 
 def bench_o_n(torch, S, stream, steps=5, warmup=3):
-    """The O(N) kernels against the HBM roofline: the OU coefficient set (implicit
-    step and explicit step are both per-particle, with grid-wide mean reductions),
-    d = 3, N = 2^26 (state 1.6 GB per array, far beyond L2), FP64 and FP32C forms.
-    Algorithmic bytes per particle-step: X read and Y written by the implicit step,
-    Y read and X written by step 2 (FP64 SoA)."""
+    """The O(N) kernels against the HBM roofline: the OU coefficient set (both steps
+    per particle: step 1 is linear in the particle, so it runs inside step 2's kernel
+    with the mean of Y from the moments of X_n), d = 3, N = 2^26 (state 1.6 GB per
+    array, far beyond L2), FP64 and FP32C forms.  Algorithmic bytes per
+    particle-step: X read, the stage Y and the new X written (FP64 SoA)."""
     peak, basis = hbm_peak_gbs()
     N = 1 << ON_LOG2N
-    out = {"workload": "OU d=3 N=2^26 h=2^-6 (k_mm_implicit + k_euler per step)",
+    out = {"workload": "OU d=3 N=2^26 h=2^-6 (one k_euler per step, step 1 fused)",
            "bytes_per_particle_step": ON_BYTES_PER_PARTICLE_STEP, "peak_gbs": peak, "peak_basis": basis}
     for name, prec in (("fp64", S.SSM_FP64), ("fp32c", S.SSM_FP32C)):
         try:
@@ -371,7 +382,7 @@ def bench_o_n(torch, S, stream, steps=5, warmup=3):
         gbs = N * ON_BYTES_PER_PARTICLE_STEP / dt / 1e9
         out[name] = {"particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3, "achieved_gbs": gbs, "frac": gbs / peak}
         s.close()
-    # the paper's moment-interaction examples, FP32C, same N (32 d bytes per particle-step)
+    # the paper's moment-interaction examples, FP32C, same N (o_n_bytes per particle-step)
     models = {}
     for name, (d, cname, p, m0, s0) in MOMENT_MODELS.items():
         coef = getattr(S, cname)
@@ -385,9 +396,10 @@ def bench_o_n(torch, S, stream, steps=5, warmup=3):
         ev[1].record(stream)
         ev[1].synchronize()
         dt = ev[0].elapsed_time(ev[1]) / 1e3 / steps
-        gbs = N * 32 * d / dt / 1e9
-        models[name] = {"d": d, "particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3, "achieved_gbs": gbs,
-                        "frac": gbs / peak}
+        gbs = N * o_n_bytes(cname, d) / dt / 1e9
+        models[name] = {"d": d, "particle_steps_per_s": N / dt, "ms_per_step": dt * 1e3,
+                        "bytes_per_particle_step": o_n_bytes(cname, d), "achieved_gbs": gbs, "frac": gbs / peak,
+                        "kernels": "k_euler (step 1 fused)" if cname in FUSED_STEP1 else "k_mm_implicit + k_euler"}
         s.close()
     out["fp32c_moment_models"] = models
     return out

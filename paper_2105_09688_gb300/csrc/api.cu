@@ -352,7 +352,8 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         return launch_euler(c, bscale);
     }
     if (is_moment(c->coef)) {
-        if ((e = launch_mm_implicit(c)) != cudaSuccess) return e;
+        // OU and the polynomial drift take step 1 inside k_euler (fused_step1)
+        if (!fused_step1(c->coef) && (e = launch_mm_implicit(c)) != cudaSuccess) return e;
         return launch_euler(c, 0.0);
     }
     // SSM_COEF_COUPLED3D / SSM_COEF_COUPLED1D

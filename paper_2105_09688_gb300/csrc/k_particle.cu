@@ -600,16 +600,55 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // only its own branch: EUL_PAIR (b from the pair partial sums, sigma per particle),
 // EUL_OU (b = lambda mean(Y), sigma = eta, the same for every particle), EUL_GEN
 // (the other moment sets: b and sigma from Y and its means, moment_b / moment_sigma).
+// S1: step 1 in the same kernel, for the sets whose step 1 is linear in the particle
+// (OU: Y = X / (1 - h rho); polynomial drift: Y = X / (1 - h gamma + h mean(X^2))).
+// Then Y = lin X needs only the moments of X_n, which the previous step (or the
+// initial state) left in mom, and so does mean(Y) = lin mean(X); the kernel reads X,
+// writes the stage Y and the new X, one pass over the state instead of two kernels
+// (k_mm_implicit, then this one) and no grid-wide reduction between them.  mean(Y)
+// differs from the sum over the Y_i by rounding only.
 enum : int { EUL_PAIR = 0, EUL_OU = 1, EUL_GEN = 2 };
 template <int D> constexpr int eul_min_blocks = D >= 2 ? EUL_MIN_BLOCKS : RED_PER_SM;
-template <int D, bool F32, int FAM>
+template <int D, bool F32, int FAM, bool S1 = false>
 __global__ void __launch_bounds__(EUL_THREADS, eul_min_blocks<D>)
-k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ part, int chunks,
-        double bscale, int coef, double p0, double p1, double p2, const double *__restrict__ ymean, int64_t N,
+k_euler(double *__restrict__ x, double *__restrict__ y, const double *__restrict__ part, int chunks,
+        double bscale, int coef, double p0, double p1, double p2, double *__restrict__ ymean, int64_t N,
         int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
         double *mpart, unsigned *ticket, double *mom, int *err, long long *counters) {
     const long long n = *dstep;
     constexpr bool GEN = FAM == EUL_GEN, OU = FAM == EUL_OU, MM = FAM != EUL_PAIR;
+    static_assert(!S1 || MM, "step 1 is fused only for the linear moment sets");
+    // S1: the factor of step 1 and mean(Y) from the moments of X_n (every block reads
+    // mom here, before its ticket; the last block overwrites it with the moments of
+    // X_{n+1} only after every block has taken one)
+    double lin = 1.0, ymd[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) ymd[c] = 0.0;
+    if (S1) {
+        lin = coef == SSM_COEF_POLY ? 1.0 / (1.0 - h * p0 + h * mom[D]) : 1.0 / (1.0 - h * p0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) ymd[c] = lin * mom[c];
+        if (blockIdx.x == 0 && threadIdx.x < D) ymean[threadIdx.x] = ymd[threadIdx.x];
+    } else if (MM) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) ymd[c] = ymean[c];
+    }
+    // Y of particle i: step 1 here (S1, also stored as the stage Y) or as step 1 left it
+    auto load_y = [&](int64_t i, double (&yv)[D]) {
+        if (S1) {
+            double xv[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) xv[c] = x[c * Np + i];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                yv[c] = xv[c] * lin;
+                y[c * Np + i] = yv[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) yv[c] = y[c * Np + i];
+        }
+    };
     // b of particle i from the pair partial sums (pair sets)
     auto pair_drift = [&](int64_t i, int c) -> double {
         double sm = 0.0;
@@ -624,8 +663,8 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
         float ymf[D], hb_ou[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            ymf[c] = MM ? (float)ymean[c] : 0.0f;
-            hb_ou[c] = OU ? (float)(h * p1 * ymean[c]) : 0.0f;
+            ymf[c] = MM ? (float)ymd[c] : 0.0f;
+            hb_ou[c] = OU ? (float)(h * p1 * ymd[c]) : 0.0f;
         }
         const float hf = (float)h, p0f = (float)p0, p1f = (float)p1, p2f = (float)p2;
         const float sqh = (float)sqrt_h, sqhf = (float)sqrt_hf;
@@ -634,11 +673,10 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
         auto advance = [&](int64_t i, float (&p)[4 * D]) {
             double yv[D];
             float yf[D], hb[D];
+            load_y(i, yv);
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                yv[c] = y[c * Np + i];
+            for (int c = 0; c < D; ++c)
                 if (!GEN) hb[c] = OU ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
-            }
 #pragma unroll
             for (int c = 0; c < D; ++c) yf[c] = f64_to_f32_fast(yv[c]);
             if (GEN)
@@ -684,11 +722,10 @@ k_euler(double *__restrict__ x, const double *__restrict__ y, const double *__re
     } else {
         double ym[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) ym[c] = MM ? ymean[c] : 0.0;
+        for (int c = 0; c < D; ++c) ym[c] = ymd[c];
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
             double yv[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) yv[c] = y[c * Np + i];
+            load_y(i, yv);
             double dw[D];
             brownian<D>(seed, i, n, sqrt_h, fine_r, sqrt_hf, dw);
 #pragma unroll
@@ -907,13 +944,22 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     const bool f32 = c->prec != SSM_FP64;
     // families by dimension: d = 1 pair sets, OU, GL/POLY/GLSTAB; d = 2 OU, CS; d = 3 pair sets, OU
     const int fam = c->coef == SSM_COEF_OU ? EUL_OU : is_moment_set(c->coef) ? EUL_GEN : EUL_PAIR;
-#define SSM_EUL(D, F, G) k_euler<D, F, G><<<red_grid(c->sms, eul_min_blocks<D>), EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, bscale, \
-        c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, c->mpart, \
-        c->ticket, c->mom, c->err, c->counters)
-#define SSM_EUL_G(D, G) { if (f32) SSM_EUL(D, true, G); else SSM_EUL(D, false, G); }
-    if (c->d == 1) { if (fam == EUL_GEN) SSM_EUL_G(1, EUL_GEN) else if (fam == EUL_OU) SSM_EUL_G(1, EUL_OU) else SSM_EUL_G(1, EUL_PAIR) }
-    else if (c->d == 2) { if (fam == EUL_GEN) SSM_EUL_G(2, EUL_GEN) else SSM_EUL_G(2, EUL_OU) }
-    else { if (fam == EUL_OU) SSM_EUL_G(3, EUL_OU) else SSM_EUL_G(3, EUL_PAIR) }
+    // OU and the polynomial drift: step 1 fused into this kernel (the caller launches
+    // no k_mm_implicit for them)
+    const bool s1 = fused_step1(c->coef);
+#define SSM_EUL(D, F, G, S) k_euler<D, F, G, S><<<red_grid(c->sms, eul_min_blocks<D>), EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, \
+        bscale, c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, \
+        c->mpart, c->ticket, c->mom, c->err, c->counters)
+#define SSM_EUL_G(D, G, S) { if (f32) SSM_EUL(D, true, G, S); else SSM_EUL(D, false, G, S); }
+    if (c->d == 1) {
+        if (fam == EUL_GEN) { if (s1) SSM_EUL_G(1, EUL_GEN, true) else SSM_EUL_G(1, EUL_GEN, false) }
+        else if (fam == EUL_OU) SSM_EUL_G(1, EUL_OU, true)
+        else SSM_EUL_G(1, EUL_PAIR, false)
+    } else if (c->d == 2) {
+        if (fam == EUL_GEN) SSM_EUL_G(2, EUL_GEN, false) else SSM_EUL_G(2, EUL_OU, true)
+    } else {
+        if (fam == EUL_OU) SSM_EUL_G(3, EUL_OU, true) else SSM_EUL_G(3, EUL_PAIR, false)
+    }
 #undef SSM_EUL_G
 #undef SSM_EUL
     k_advance<<<1, 1, 0, c->st>>>(c->dstep, c->counters, c->N);
