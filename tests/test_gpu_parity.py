@@ -252,6 +252,38 @@ def test_autotune_changes_shape_not_results(S):
     assert np.max(np.abs(runs[0] - runs[1])) < K * 2 * 64 * tol
 
 
+@pytest.mark.parametrize("chunks", [1, 2, 5, 40])
+def test_source_chunks_change_grouping_not_results(S, chunks):
+    """A pair pass splits the sources of every target tile into chunks, one set of
+    partial sums each, added by the consumer in chunk order.  With another chunk
+    count (ssm_opts.tile_chunks; 40 is capped at one 512-source sub-tile a chunk, and
+    the step-1 passes over part of the particles re-pack their blocks into more
+    chunks) the sums are grouped differently, but the step-1 roots pass the same
+    residual test and the drift is the same to rounding: the first step's Y within
+    1e-9 of the planned launch's, b within 1e-12, the state after 3 steps within
+    3 x 2 x 64 tol (N = 3000: a ragged last tile and a ragged last chunk)."""
+    N, h, K = 3000, 2.0 ** -8, 3
+    out = []
+    for k in (0, chunks):
+        s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=13, precision=S.SSM_FP32C, tile_chunks=k)
+        s.set_plan(0, 2, 128, 4)
+        s.set_plan(1, 2, 128, 8)
+        if k:   # chunks of whole 512-source sub-tiles, at most one per 256 sources
+            want = min(k, -(-N // 256))
+            length = -(-(-(-N // want)) // 512) * 512
+            assert s.plan(0)["chunks"] == -(-N // length)
+        s.step()
+        y, b = s.get_stage(S.SSM_STAGE_Y), s.get_stage(S.SSM_STAGE_B)
+        s.run_steps(K - 1)
+        out.append((y, b, s.get_state()[0]))
+        s.close()
+    (y0, b0, x0), (y1, b1, x1) = out
+    tol = max(1e-10, 2.0 ** -27 * h * (1.0 + 64.0 / math.sqrt(N)))
+    assert np.max(np.abs(y0 - y1)) < 1e-9
+    assert np.max(np.abs(b0 - b1)) < 1e-12 * max(1.0, np.abs(b0).max())
+    assert np.max(np.abs(x0 - x1)) < K * 2 * 64 * tol
+
+
 def test_set_plan_rejects_unknown_shape(S):
     s = S.SSM(d=3, N=100, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=1)   # FP64: no packed kernels
     with pytest.raises(S.SSMError):
