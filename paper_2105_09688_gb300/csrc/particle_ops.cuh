@@ -98,10 +98,16 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
     local_root<D>(S, Sw, Y, X, h, u);
     // Residual bound at u without another pair pass.  G(u) = 0 is the local model;
     // r(u) - G(u) = -h/2 (S(u) - S(Y) + Sw (u - Y)), and by the mean value theorem
-    // |S(u) - S(Y) + Sw (u - Y)| <= (||2 M2|| + |grad Sw| |u - Y|) |u - Y| with
-    // M2 = (1/N) sum_j w_j^2 d_j d_j^T, ||2 M2|| <= 2 max_r r^2/(1+r^2)^2 = 1/2 and
-    // |grad Sw| <= 2 max_r r/(1+r^2)^2 < 0.65.  When the bound is within tol the
-    // particle is done at u (S is moved to u to first order for the record).
+    // |S(u) - S(Y) + Sw (u - Y)| <= (max_z ||2 M2(z)|| + |grad Sw| |u - Y|) |u - Y|
+    // over z on the segment from Y to u, with M2 = (1/N) sum_j w_j^2 d_j d_j^T and
+    // |grad Sw| <= 2 max_r r/(1+r^2)^2 < 0.65.  M2 is positive semidefinite, so
+    // ||2 M2|| <= 2 tr M2 = (2/N) sum_j w_j^2 |d_j|^2 = (2/N) sum_j w_j (1 - w_j)
+    // (w |d|^2 = 1 - w), and (1/N) sum_j w_j^2 >= Sw^2 (Cauchy-Schwarz), so
+    // ||2 M2|| <= 2 Sw (1 - Sw) <= 1/2: small where the sum is dominated by near
+    // (Sw -> 1) or by far (Sw -> 0) sources.  Along the segment Sw moves by at most
+    // 0.65 |u - Y| and s (1 - s) has slope at most 1, hence m2 below (1e-6 covers the
+    // rounding of the FP32 pair sum and its FP32 target).  When the bound is within
+    // tol the particle is done at u (S is moved to u to first order for the record).
     double uu = 0.0, du2 = 0.0, ginf = 0.0;
 #pragma unroll
     for (int c = 0; c < D; ++c) uu += u[c] * u[c];
@@ -113,7 +119,8 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
         du2 += du * du;
     }
     const double dn = sqrt(du2);
-    const double bound = 0.5 * h * (0.5 + 0.65 * dn) * dn + ginf;
+    const double m2 = fmin(0.5, 2.0 * Sw * (1.0 - Sw) + 1.3 * dn + 1e-6);
+    const double bound = 0.5 * h * (m2 + 0.65 * dn) * dn + ginf;
     if (bound <= tol) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {

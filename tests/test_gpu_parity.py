@@ -259,9 +259,10 @@ def test_source_chunks_change_grouping_not_results(S, chunks):
     count (ssm_opts.tile_chunks; 40 is capped at one 512-source sub-tile a chunk, and
     the step-1 passes over part of the particles re-pack their blocks into more
     chunks) the sums are grouped differently, but the step-1 roots pass the same
-    residual test and the drift is the same to rounding: the first step's Y within
-    1e-9 of the planned launch's, b within 1e-12, the state after 3 steps within
-    3 x 2 x 64 tol (N = 3000: a ragged last tile and a ragged last chunk)."""
+    residual test: the first step's Y within 1e-9 of the planned launch's; b, the
+    FP32 drift at those two Y (each within 5e-7 of the oracle's, the bound of
+    test_coupled3d_fp32c_every_launch_shape), within 1e-6; the state after 3 steps
+    within 3 x 2 x 64 tol (N = 3000: a ragged last tile and a ragged last chunk)."""
     N, h, K = 3000, 2.0 ** -8, 3
     out = []
     for k in (0, chunks):
@@ -280,7 +281,7 @@ def test_source_chunks_change_grouping_not_results(S, chunks):
     (y0, b0, x0), (y1, b1, x1) = out
     tol = max(1e-10, 2.0 ** -27 * h * (1.0 + 64.0 / math.sqrt(N)))
     assert np.max(np.abs(y0 - y1)) < 1e-9
-    assert np.max(np.abs(b0 - b1)) < 1e-12 * max(1.0, np.abs(b0).max())
+    assert np.max(np.abs(b0 - b1)) < 1e-6
     assert np.max(np.abs(x0 - x1)) < K * 2 * 64 * tol
 
 
