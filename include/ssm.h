@@ -324,6 +324,14 @@ ssm_status ssm_get_plan(ssm_ctx *ctx, int which, int *out);
  * SSM_EINVAL if that shape is not compiled for the context's pair kind/precision. */
 ssm_status ssm_set_plan(ssm_ctx *ctx, int which, const int *in);
 
+/* The same with the source chunk count fixed: in[4] = {form, threads per block,
+ * targets per thread, chunks >= 1 (at most the context's cap: one chunk per 256
+ * sources, at most 32, and the partial-sum scratch)}.  ssm_get_plan's out[0..3] of a
+ * tuned context, given back here, restore its plan exactly (the chunk length is a
+ * function of N, the shape and the chunk count), which is how a tuning cache skips
+ * the autotuner.  SSM_EINVAL for an unknown shape or a chunk count out of range. */
+ssm_status ssm_set_plan_chunks(ssm_ctx *ctx, int which, const int *in);
+
 /* ---- batched form: many independent ensembles in one graph launch ----
  * Each ensemble is the coupled coefficient set (SSM_COEF_COUPLED3D formulas) at
  * d = 1 or d = 3, with its own N, h, T, seed and Brownian grid, stepped by the SSM

@@ -23,7 +23,7 @@ __all__ = [
     "ssm_opts_default", "ssm_workspace_bytes", "ssm_create", "ssm_step", "ssm_run_steps", "ssm_run", "ssm_sync",
     "ssm_moments", "ssm_get_state", "ssm_set_state", "ssm_get_stage", "ssm_stats", "ssm_destroy",
     "ssm_status_str", "ssm_philox", "ssm_normals", "ssm_normals_fp32", "ssm_convert_check", "ssm_cardano", "ssm_pair_pass", "ssm_autotune", "ssm_get_plan",
-    "ssm_set_plan", "ssm_drift_noalloc", "ssm_pipe_probe", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "SSM_COEF_GLSTAB", "ssm_stability_beta", "load_ws",
+    "ssm_set_plan", "ssm_set_plan_chunks", "tune_cache_key", "tune_cache_load", "tune_cache_store", "ssm_drift_noalloc", "ssm_pipe_probe", "SSM", "Batch", "ssm_ens_desc", "SSM_COEF_COUPLED1D", "SSM_COEF_GL1", "SSM_COEF_GL2", "SSM_COEF_POLY", "SSM_COEF_CS", "SSM_COEF_GLSTAB", "ssm_stability_beta", "load_ws",
     "ssm_ws_train", "ssm_ws_predict", "ssm_ws_grad", "ssm_ws_collect", "ssm_ws_load", "ssm_ws_params", "ssm_ws_blob_bytes",
     "ssm_ws_num_params",
 ]
@@ -101,6 +101,7 @@ _SIGS = {
     "ssm_autotune": (_i32, [_vp, _DP]),
     "ssm_get_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ssm_set_plan": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+    "ssm_set_plan_chunks": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ssm_drift_noalloc": (_i32, [_i32, _i32, _i64, _vp, _i64, _vp, _vp]),
     "ssm_ws_blob_bytes": (_sz, []),
     "ssm_ws_num_params": (_i32, []),
@@ -456,6 +457,59 @@ def ssm_set_plan(ctx, which, form, threads, targets_per_thread):
     _check(lib().ssm_set_plan(ctx, int(which), arr), "ssm_set_plan")
 
 
+def ssm_set_plan_chunks(ctx, which, form, threads, targets_per_thread, chunks):
+    """ssm_set_plan with the source chunk count fixed (chunks >= 1)."""
+    arr = (_i32 * 4)(int(form), int(threads), int(targets_per_thread), int(chunks))
+    _check(lib().ssm_set_plan_chunks(ctx, int(which), arr), "ssm_set_plan_chunks")
+
+
+# Tuning cache: the autotuner's choice per device, library build and workload, kept
+# in a JSON file so that later contexts of the same workload take it without tuning.
+def tune_cache_key(device_name, sms, library_digest, d, N, coef, precision):
+    """Key of a tuned plan: the device (name, SM count), the library build (a digest
+    of libssm.so) and the workload (d, N, coefficient set, precision)."""
+    return "|".join(str(v) for v in (device_name, int(sms), library_digest, int(d), int(N), int(coef),
+                                     int(precision)))
+
+
+def tune_cache_load(path):
+    """The cache's entries ({} if the file is missing or not a JSON object)."""
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return data if isinstance(data, dict) else {}
+
+
+def tune_cache_store(path, key, entry):
+    """Adds or replaces one entry; the file is rewritten through a temporary file in
+    the same directory and renamed over the old one, so readers see either file."""
+    import json
+    import tempfile
+    data = tune_cache_load(path)
+    data[key] = entry
+    d = os.path.dirname(os.path.abspath(path))
+    fd, tmp = tempfile.mkstemp(prefix=".tune", dir=d)
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
+
+
+def _library_digest():
+    import hashlib
+    h = hashlib.sha256()
+    with open(LIB_PATH, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def ssm_drift_noalloc(coef, precision, N, y_ptr, ld, b_ptr, stream_ptr=0):
     """Step-2 drift of the device arrays at y_ptr into b_ptr (SoA, leading dimension ld)
     without allocating (scratch is a fixed static device array; see include/ssm.h).
@@ -527,14 +581,42 @@ class SSM:
     def pair_pass(self, which):
         return ssm_pair_pass(self.ctx, which)
 
-    def autotune(self):
-        return ssm_autotune(self.ctx)
+    def autotune(self, cache=None):
+        """Tune the pair-sum launch shapes; returns the best pass times [step 1, drift]
+        in ms.  cache: path of a JSON tuning cache: a plan tuned earlier for this
+        device, library build and workload (d, N, coefficient set, precision) is
+        restored with ssm_set_plan_chunks instead of tuning (its recorded times are
+        returned), and a newly tuned one is added to the file."""
+        pair_kinds = {SSM_COEF_COUPLED3D: (0, 1), SSM_COEF_COUPLED1D: (0, 1), SSM_COEF_CUBIC1D_GAUSS: (1,)}
+        if cache is None or self.coef not in pair_kinds:
+            return ssm_autotune(self.ctx)
+        import torch
+        dev = torch.cuda.current_device()
+        key = tune_cache_key(torch.cuda.get_device_name(dev), torch.cuda.get_device_properties(dev).multi_processor_count,
+                             _library_digest(), self.d, self.N, self.coef, self.opts.precision)
+        entry = tune_cache_load(cache).get(key)
+        if entry:
+            try:
+                for which, p in enumerate(entry["plans"]):
+                    if p is not None:
+                        self.set_plan(which, p["form"], p["threads"], p["targets_per_thread"], chunks=p["chunks"])
+                return np.array(entry["best_ms"], dtype=float)
+            except (KeyError, TypeError, SSMError):
+                pass   # an entry this library cannot take: tune afresh
+        best = ssm_autotune(self.ctx)
+        plans = [self.plan(which) if which in pair_kinds[self.coef] else None for which in (0, 1)]
+        tune_cache_store(cache, key, {"plans": plans, "best_ms": [float(v) for v in best]})
+        return best
 
     def plan(self, which):
         return ssm_get_plan(self.ctx, which)
 
-    def set_plan(self, which, form, threads, targets_per_thread):
-        ssm_set_plan(self.ctx, which, form, threads, targets_per_thread)
+    def set_plan(self, which, form, threads, targets_per_thread, chunks=0):
+        """chunks: 0 = planned (or ssm_opts.tile_chunks); >= 1 fixes the source chunks."""
+        if chunks:
+            ssm_set_plan_chunks(self.ctx, which, form, threads, targets_per_thread, chunks)
+        else:
+            ssm_set_plan(self.ctx, which, form, threads, targets_per_thread)
 
     def ws_load(self, blob):
         ssm_ws_load(self.ctx, blob)

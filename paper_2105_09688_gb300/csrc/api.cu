@@ -817,11 +817,14 @@ ssm_status ssm_get_plan(ssm_ctx *c, int which, int *out) {
     return SSM_OK;
 }
 
-ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
+// A compiled shape {form, threads, targets per thread} with `chunks` source chunks
+// (0: planned from the device's slots, or ssm_opts.tile_chunks).
+static ssm_status set_plan_shape(ssm_ctx *c, int which, const int *in, int chunks) {
     if (!c || !in || (which != 0 && which != 1)) return SSM_EINVAL;
     if (is_moment(c->coef) || (which == 0 && !is_coupled(c->coef))) return SSM_EINVAL;
     const bool f32 = fp32_pairs(c);
     const int kind = which == 0 ? newton_kind(c->d) : drift_kind(c->coef);
+    if (chunks < 0 || chunks > chunks_cap(c->N, kind_nc(kind))) return SSM_EINVAL;
     int cand[32][3];
     const int nc = pair_shape_candidates(kind, f32, cand, 32);
     bool ok = false;
@@ -829,10 +832,18 @@ ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) {
         if (cand[k][0] == in[0] && cand[k][1] == in[1] && cand[k][2] == in[2]) ok = true;
     if (!ok) return SSM_EINVAL;
     const int slots = device_slots(kind, f32, in[0], in[1], in[2]);
-    Plan p = make_plan_shape(c->N, kind, in[0], in[1], in[2], c->opt.tile_chunks, slots);
+    Plan p = make_plan_shape(c->N, kind, in[0], in[1], in[2], chunks > 0 ? chunks : c->opt.tile_chunks, slots);
     if (which == 0) c->plan_newton = p; else c->plan_drift = p;
     if (c->graph_ready) { cudaGraphExecDestroy(c->gexec); c->graph_ready = false; }
     return SSM_OK;
+}
+
+ssm_status ssm_set_plan(ssm_ctx *c, int which, const int *in) { return set_plan_shape(c, which, in, 0); }
+
+ssm_status ssm_set_plan_chunks(ssm_ctx *c, int which, const int *in) {
+    if (!in) return SSM_EINVAL;
+    if (in[3] < 1) return SSM_EINVAL;
+    return set_plan_shape(c, which, in, in[3]);
 }
 
 ssm_status ssm_cardano(const double *x, int64_t n, double h, double *y) {

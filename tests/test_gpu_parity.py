@@ -285,6 +285,38 @@ def test_source_chunks_change_grouping_not_results(S, chunks):
     assert np.max(np.abs(x0 - x1)) < K * 2 * 64 * tol
 
 
+def test_tuning_cache_restores_the_tuned_plan(S, tmp_path):
+    """A second context of the same workload takes the tuned plans from the JSON cache
+    (ssm_set_plan_chunks, no tuning): the same shapes and chunk counts, and the same
+    states bit for bit after a few steps."""
+    N, h, K = 5000, 2.0 ** -8, 2
+    cache = str(tmp_path / "tune.json")
+    runs = []
+    for _ in range(2):
+        s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=14, precision=S.SSM_FP32C)
+        best = s.autotune(cache=cache)
+        assert np.all(best > 0)
+        plans = (s.plan(0), s.plan(1))
+        s.run_steps(K)
+        runs.append((plans, s.get_state()[0]))
+        s.close()
+    assert len(S.tune_cache_load(cache)) == 1
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_set_plan_chunks_rejects_out_of_range(S):
+    s = S.SSM(d=3, N=3000, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=1, precision=S.SSM_FP32C)
+    for bad in (0, -1, 10 ** 6):
+        with pytest.raises(S.SSMError):
+            S.ssm_set_plan_chunks(s.ctx, 0, 2, 128, 4, bad)
+    with pytest.raises(S.SSMError):
+        S.ssm_set_plan_chunks(s.ctx, 0, 2, 96, 4, 3)   # not a compiled shape
+    s.set_plan(0, 2, 128, 4, chunks=3)
+    assert s.plan(0)["chunks"] == 3
+    s.close()
+
+
 def test_set_plan_rejects_unknown_shape(S):
     s = S.SSM(d=3, N=100, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=1)   # FP64: no packed kernels
     with pytest.raises(S.SSMError):
