@@ -129,7 +129,8 @@ __device__ __forceinline__ double cardano_root_a(double x, double h, double a) {
 __device__ __forceinline__ double cardano_root(double x, double h) { return cardano_root_a(x, h, 1.0 - h); }
 
 // The root of h y^3 + a y = x + c for the FP32C forms (c: GL2's measure term, else
-// 0).  The Cardano form in FP32 gives y0 (relative error ~1e-7); one Newton
+// 0).  The Cardano form in FP32 gives y0 (relative error ~1e-7; its cube root and
+// square root on the special-function unit); one Newton
 // correction y0 - f(y0) / f'(y0) follows, with the residual f = h y0^3 + a y0 - x - c
 // evaluated in double-float arithmetic on the FP32 pipe (error-free products by FMA
 // and Knuth's two-sum; x split into two floats on the integer pipes, h, a and c
@@ -164,7 +165,13 @@ __device__ __forceinline__ double cardano32_a(double x, const Cubic32 &k) {
     const float xs = SHIFT ? xh + k.c_hi : xh;
     const float q = -xs * k.ih;
     const float disc = fmaf(0.25f * q, q, k.p3 * k.p3 * k.p3);
-    float u = cbrtf(0.5f * fabsf(q) + sqrtf(disc));
+    // u = cbrt(cv), cv = |q|/2 + sqrt(disc) >= p3^(3/2) > 0 (a normal float):
+    // 2^(log2(cv)/3) on the special-function unit (~3e-7 relative), then one Newton step
+    // for the cube root, u <- (2u + cv/u^2)/3, to FP32 rounding; the square root's ~2^-22
+    // only moves cv, which the correction of the cubic's root below absorbs
+    const float cv = fmaf(0.5f, fabsf(q), sqrt_approx(disc));
+    float u = ex2_approx(lg2_approx(cv) * (1.0f / 3.0f));
+    u = (2.0f * u + cv * (rcp_approx(u * u))) * (1.0f / 3.0f);
     if (q > 0.0f) u = -u;
     const float w = __fdividef(-k.p3, u);
     const float y0 = __fdividef(-q, fmaf(u, u, k.p3) + w * w);
