@@ -616,12 +616,15 @@ __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *c
 // differs from the sum over the Y_i by rounding only.
 enum : int { EUL_PAIR = 0, EUL_OU = 1, EUL_GEN = 2 };
 template <int D> constexpr int eul_min_blocks = D >= 2 ? EUL_MIN_BLOCKS : RED_PER_SM;
-template <int D, bool F32, int FAM, bool S1 = false>
+// CF: the coefficient set fixed at compile time (the EUL_GEN instances, so that the
+// per-particle b and sigma carry no switch over the sets), or -1 to take `coef`.
+template <int D, bool F32, int FAM, bool S1 = false, int CF = -1>
 __global__ void __launch_bounds__(EUL_THREADS, eul_min_blocks<D>)
 k_euler(double *__restrict__ x, double *__restrict__ y, const double *__restrict__ part, int chunks,
-        double bscale, int coef, double p0, double p1, double p2, double *__restrict__ ymean, int64_t N,
+        double bscale, int coef_arg, double p0, double p1, double p2, double *__restrict__ ymean, int64_t N,
         int64_t Np, double h, double sqrt_h, int fine_r, double sqrt_hf, uint64_t seed, long long *dstep,
         double *mpart, unsigned *ticket, double *mom, int *err, long long *counters) {
+    const int coef = CF >= 0 ? CF : coef_arg;
     const long long n = *dstep;
     constexpr bool GEN = FAM == EUL_GEN, OU = FAM == EUL_OU, MM = FAM != EUL_PAIR;
     static_assert(!S1 || MM, "step 1 is fused only for the linear moment sets");
@@ -954,18 +957,22 @@ cudaError_t launch_euler(ssm_ctx *c, double bscale) {
     // OU and the polynomial drift: step 1 fused into this kernel (the caller launches
     // no k_mm_implicit for them)
     const bool s1 = fused_step1(c->coef);
-#define SSM_EUL(D, F, G, S) k_euler<D, F, G, S><<<red_grid(c->sms, eul_min_blocks<D>), EUL_THREADS, 0, c->st>>>(c->x, c->y, c->part, chunks, \
-        bscale, c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, c->dstep, \
-        c->mpart, c->ticket, c->mom, c->err, c->counters)
-#define SSM_EUL_G(D, G, S) { if (f32) SSM_EUL(D, true, G, S); else SSM_EUL(D, false, G, S); }
+#define SSM_EUL(D, F, G, S, CF) k_euler<D, F, G, S, CF><<<red_grid(c->sms, eul_min_blocks<D>), EUL_THREADS, 0, c->st>>>(c->x, c->y, \
+        c->part, chunks, bscale, c->coef, p0, p1, p2, c->ymean, c->N, c->Np, c->h, sqrt(c->h), fine_r, sqrt_hf, c->seed, \
+        c->dstep, c->mpart, c->ticket, c->mom, c->err, c->counters)
+#define SSM_EUL_G(D, G, S, CF) { if (f32) SSM_EUL(D, true, G, S, CF); else SSM_EUL(D, false, G, S, CF); }
     if (c->d == 1) {
-        if (fam == EUL_GEN) { if (s1) SSM_EUL_G(1, EUL_GEN, true) else SSM_EUL_G(1, EUL_GEN, false) }
-        else if (fam == EUL_OU) SSM_EUL_G(1, EUL_OU, true)
-        else SSM_EUL_G(1, EUL_PAIR, false)
+        if (fam == EUL_GEN) {
+            if (c->coef == SSM_COEF_POLY) SSM_EUL_G(1, EUL_GEN, true, SSM_COEF_POLY)
+            else if (c->coef == SSM_COEF_GL1) SSM_EUL_G(1, EUL_GEN, false, SSM_COEF_GL1)
+            else if (c->coef == SSM_COEF_GL2) SSM_EUL_G(1, EUL_GEN, false, SSM_COEF_GL2)
+            else SSM_EUL_G(1, EUL_GEN, false, -1)   // GLSTAB
+        } else if (fam == EUL_OU) SSM_EUL_G(1, EUL_OU, true, -1)
+        else SSM_EUL_G(1, EUL_PAIR, false, -1)
     } else if (c->d == 2) {
-        if (fam == EUL_GEN) SSM_EUL_G(2, EUL_GEN, false) else SSM_EUL_G(2, EUL_OU, true)
+        if (fam == EUL_GEN) SSM_EUL_G(2, EUL_GEN, false, SSM_COEF_CS) else SSM_EUL_G(2, EUL_OU, true, -1)
     } else {
-        if (fam == EUL_OU) SSM_EUL_G(3, EUL_OU, true) else SSM_EUL_G(3, EUL_PAIR, false)
+        if (fam == EUL_OU) SSM_EUL_G(3, EUL_OU, true, -1) else SSM_EUL_G(3, EUL_PAIR, false, -1)
     }
 #undef SSM_EUL_G
 #undef SSM_EUL
