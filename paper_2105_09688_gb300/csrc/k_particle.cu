@@ -199,7 +199,9 @@ __device__ __forceinline__ double cardano32_a(double x, const Cubic32 &k) {
     two_sum(t, r, v, ve);
     const float f = v + ((ve + te + ce) + (rl + sl - xl - (SHIFT ? k.c_lo : 0.0f)));
     const float fp = fmaf(3.0f * k.hf * y0, y0, k.af);
-    return f32_to_f64(y0) - f32_to_f64(__fdividef(f, fp));
+    // the FP64 result with the hardware conversions: this kernel's integer pipe is the
+    // busier one (the bit-level conversions and splits), its FP64 pipe the idler
+    return (double)y0 - (double)__fdividef(f, fp);
 }
 
 __global__ void k_cardano(const double *__restrict__ x, double *__restrict__ y, int64_t n, double h) {
