@@ -700,7 +700,9 @@ k_euler(double *__restrict__ x, double *__restrict__ y, const double *__restrict
             for (int c = 0; c < D; ++c) {
                 const float sg = GEN ? moment_sigma<float>(coef, c, yf, ymf, p0f, p1f, p2f) : OU ? p2f : sigma_of32(coef, yf[c], p2f);
                 const float inc = fmaf(sg, dw[c], hb[c]);
-                x[c * Np + i] = yv[c] + f32_to_f64(inc);
+                // at d <= 2 the FP64 pipe has room for the hardware conversion, which
+                // frees the integer pipe; at d = 3 (three adds a particle) it does not
+                x[c * Np + i] = yv[c] + (D <= 2 ? (double)inc : f32_to_f64(inc));
                 const float v = yf[c] + inc, v2 = v * v;
                 p[0 * D + c] = v;
                 p[1 * D + c] = v2;
