@@ -690,7 +690,8 @@ k_euler(double *__restrict__ x, double *__restrict__ y, const double *__restrict
             for (int c = 0; c < D; ++c)
                 if (!GEN) hb[c] = OU ? hb_ou[c] : hf * f64_to_f32(pair_drift(i, c));
 #pragma unroll
-            for (int c = 0; c < D; ++c) yf[c] = f64_to_f32_fast(yv[c]);
+            for (int c = 0; c < D; ++c)   // the d = 1 sets with step 1 in its own kernel: FP64 pipe to spare
+                yf[c] = (D == 1 && GEN && !S1) ? (float)yv[c] : f64_to_f32_fast(yv[c]);
             if (GEN)
 #pragma unroll
                 for (int c = 0; c < D; ++c) hb[c] = hf * moment_b<float>(coef, c, yf, ymf, p0f, p1f);
