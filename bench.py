@@ -652,22 +652,28 @@ def main():
         ws_forward["default"] = "mma_sync_bf16"
 
     # the same FP32C form without the learned start (same launch shapes, same timing)
-    fp32c_plain = None
-    if form.startswith("learned"):
+    # the FP32C form without the learned start, from the plain start Y = X and from the
+    # carried start (ssm_opts.carry_start: the previous step's converged pair sums), on
+    # the tuned shapes and chunk counts, timed like the headline
+    def fp32c_form(carry):
         q = S.SSM(d=DIM, N=N_PART, h=H, T=T_END, coef=S.SSM_COEF_COUPLED3D, seed=seed, stream=stream,
-                  precision=S.SSM_FP32C)
+                  precision=S.SSM_FP32C, carry_start=carry)
         for w in (0, 1):
             pl = plans["step1_pairs" if w == 0 else "drift_pairs"]
-            q.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"])
+            q.set_plan(w, pl["form"], pl["threads"], pl["targets_per_thread"], chunks=pl["chunks"])
         for _ in range(args.warmup + 1):
             q.run_steps(1)
         q.sync()
         qt_s, _, qrows, _, _ = time_spread_steps(torch, q, stream, flush, args.steps, int(round(T_END / H)))
         qt = sum(qt_s)
-        fp32c_plain = {"value": N_PART * args.steps / qt, "unit": "particle-steps/s",
-                       "ms_per_step": 1e3 * qt / args.steps,
-                       "newton_rows_per_step": sum(qrows) / args.steps}
         q.close()
+        return {"value": N_PART * args.steps / qt, "unit": "particle-steps/s", "ms_per_step": 1e3 * qt / args.steps,
+                "newton_rows_per_step": sum(qrows) / args.steps}
+
+    fp32c_plain = fp32c_carried = None
+    if form.startswith("learned"):
+        fp32c_plain = fp32c_form(0)
+        fp32c_carried = fp32c_form(1)
 
     # plain FP64 GPU SSM on the same workload (comparison of the metric): its own
     # launch shapes (tuned on the same workload at N = 2^16, where a pass takes 1/16 of
@@ -744,6 +750,7 @@ def main():
                        "plans": plans},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(round(launches_per_step * args.steps)),
             "fp32c_without_learned_start": fp32c_plain,
+            "fp32c_carried_start": fp32c_carried,
             "fallbacks_per_step": (st1["fallbacks"] - st0["fallbacks"]) / max(1, st1["steps"] - st0["steps"]),
             "plain_fp64": fp64,
             "batched_form": batched,

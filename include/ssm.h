@@ -146,6 +146,14 @@ typedef struct {
                                N not a multiple of 128, so the index lies inside the padded
                                arrays) for the bounds checks to report as SSM_EBOUNDS.  Must be 0
                                otherwise (SSM_EINVAL). */
+    int carry_start;        /* coupled sets, SSM_FP64 and SSM_FP32C, step 1 against mu^X: 0
+                               (default) = step 1 starts at Y = X; 1 = from the second step of
+                               a run on (and after ssm_set_state at the same step index) it
+                               starts at the root of u = X + h(-u|u|^2 + S* / 2), S* the
+                               particle's converged pair sum of the previous step: a warm start
+                               of the same solve (no counterpart in the paper), the roots are
+                               certified to newton_tol as before, about one pass fewer.
+                               SSM_EINVAL with other sets, forms or measure_y. */
 } ssm_opts;
 
 typedef struct {

@@ -56,7 +56,8 @@ class ssm_opts(ctypes.Structure):
     _fields_ = [("precision", _i32), ("newton_tol", _dbl), ("newton_kmax", _i32), ("fine_log2", _i32),
                 ("x0_mean", _dbl), ("x0_std", _dbl), ("coef_params", _dbl * 4), ("stream", _vp),
                 ("workspace", _vp), ("workspace_bytes", _sz), ("tile_chunks", _i32), ("ws_passes", _i32),
-                ("measure_y", _i32), ("ws_forward", _i32), ("fixed_pass_launches", _i32), ("inject", _i32)]
+                ("measure_y", _i32), ("ws_forward", _i32), ("fixed_pass_launches", _i32), ("inject", _i32),
+                ("carry_start", _i32)]
 
 
 class ssm_stats_t(ctypes.Structure):

@@ -32,6 +32,7 @@ cudaError_t launch_normals(uint64_t seed, int d, int64_t N, uint32_t step, uint3
 cudaError_t launch_normals32(uint64_t seed, int d, int64_t N, uint32_t step, uint32_t stream, float *out,
                              cudaStream_t st);
 cudaError_t ws_forward_start(ssm_ctx *c);
+cudaError_t launch_carry_start(ssm_ctx *c);
 }  // namespace ssm
 
 namespace ssm {
@@ -265,6 +266,9 @@ ssm_status check_args(int d, int64_t N, double h, double T, int coef, const ssm_
     if (o.tile_chunks < 0 || o.fixed_pass_launches < 0 || o.fixed_pass_launches > 1 || o.ws_forward < 0 ||
         o.ws_forward > 1)
         return SSM_EINVAL;
+    if (o.carry_start != 0 && (o.carry_start != 1 || !is_coupled(coef) || o.measure_y ||
+                               o.precision == SSM_FP32C_LEARNED))
+        return SSM_EINVAL;
     // ssm_opts.inject: only in the debug build, only the planted list entry of step 1
     // (coupled sets against mu^X) at an N whose padded arrays extend past particle N
 #ifdef SSM_CHECK_BOUNDS
@@ -370,6 +374,8 @@ cudaError_t enqueue_step(ssm_ctx *c) {
         if ((e = launch_newton_begin(c)) != cudaSuccess) return e;
         if (c->prec == SSM_FP32C_LEARNED && c->ws_loaded)
             if ((e = ws_forward_start(c)) != cudaSuccess) return e;
+        if (c->opt.carry_start)
+            if ((e = launch_carry_start(c)) != cudaSuccess) return e;
         if (c->opt.fixed_pass_launches) {
             for (int k = 0; k < c->kmax; ++k) {
                 if ((e = pair_sums(newton_kind(c->d), f32, c->plan_newton, c->x, c->y, (k & 1) ? c->act1 : c->act0,

@@ -135,35 +135,37 @@ __device__ __forceinline__ void forward(const Net &n, const float *f, float *out
 // reciprocal for 1/a and 1/(a + 2h|u|^2)); FP32 on the small increment is far more
 // accurate than the start needs (the prediction itself is good to ~1e-6), and the FP64
 // state keeps X exact.  A non-finite result leaves the plain start Y = X.
-__device__ __forceinline__ void cubic_start(const double (&X)[3], const float (&S)[3], double h, double *yi,
+template <int D>
+__device__ __forceinline__ void cubic_start(const double (&X)[D], const float (&S)[D], double h, double *yi,
                                             int64_t Np) {
     const float hf = (float)h;
-    float xf[3], s2[3], dl[3];
+    float xf[D], s2[D], dl[D];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { xf[c] = f64_to_f32_fast(X[c]); s2[c] = 0.5f * hf * S[c]; dl[c] = 0.0f; }
+    for (int c = 0; c < D; ++c) { xf[c] = f64_to_f32_fast(X[c]); s2[c] = 0.5f * hf * S[c]; dl[c] = 0.0f; }
     for (int it = 0; it < 10; ++it) {
-        float u[3], g[3];
+        float u[D], g[D], uu = 0.0f, ug = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) u[c] = xf[c] + dl[c];
-        const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        for (int c = 0; c < D; ++c) { u[c] = xf[c] + dl[c]; uu += u[c] * u[c]; }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) g[c] = dl[c] + hf * u[c] * uu - s2[c];
+        for (int c = 0; c < D; ++c) { g[c] = dl[c] + hf * u[c] * uu - s2[c]; ug += u[c] * g[c]; }
         const float a = 1.0f + hf * uu, b = a + 2.0f * hf * uu;
         const float r = 1.0f / (a * b);
-        const float ia = b * r, f = 2.0f * hf * (u[0] * g[0] + u[1] * g[1] + u[2] * g[2]) * (a * r);
+        const float ia = b * r, f = 2.0f * hf * ug * (a * r);
         float smax = 0.0f, dmax = 0.0f;
+        bool fin = true;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < D; ++c) {
             const float st = (g[c] - f * u[c]) * ia;
             dl[c] -= st;
             smax = fmaxf(smax, fabsf(st));
             dmax = fmaxf(dmax, fabsf(dl[c]));
+            fin = fin && isfinite(dl[c]);
         }
+        if (!fin) return;   // a non-finite result leaves the plain start
         if (smax <= 1e-7f * dmax) break;
     }
-    if (isfinite(dl[0]) && isfinite(dl[1]) && isfinite(dl[2]))
 #pragma unroll
-        for (int c = 0; c < 3; ++c) yi[c * Np] = X[c] + f32_to_f64(dl[c]);
+    for (int c = 0; c < D; ++c) yi[c * Np] = X[c] + f32_to_f64(dl[c]);
 }
 
 // The prediction used for the start: the network's S_pred, plus -- when the previous
@@ -184,7 +186,7 @@ __device__ __forceinline__ void corrected_start(const double (&X)[3], const floa
         if (corr) Su[c] += f64_to_f32_fast(sconv[c * Np + i] - (double)spred[c * Np + i]);
         spred[c * Np + i] = S[c];
     }
-    cubic_start(X, Su, h, y + i, Np);
+    cubic_start<3>(X, Su, h, y + i, Np);
 }
 
 // Learned start of step 1 on the CUDA cores (FFMA, weights broadcast from shared memory).
@@ -578,6 +580,37 @@ cudaError_t set_smem_limits() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NET_SMEM);
     if (e == cudaSuccess) done = true;
     return e;
+}
+
+// Start of step 1 from the previous step's converged pair sums (ssm_opts.carry_start;
+// no counterpart in the paper, a warm start of the same solve): from the second step
+// of a run on, Y_i starts at the root of u = X_i + h(-u|u|^2 + S*_i / 2), S*_i the
+// particle's converged pair sum of the previous step (sconv), which the step's own sum
+// differs from by how far the particle and the measure moved in one step -- O(sqrt h),
+// so the start is ~1e-5 from the root instead of h|v(X_i)| ~ 1e-2 for Y = X, and
+// step 1 needs one pass less.  *valid == 0 (the first step, or a state that was set)
+// keeps the plain start that k_newton_begin wrote.
+template <int D>
+__global__ void k_carry_start(const double *__restrict__ x, double *__restrict__ y, const double *__restrict__ sconv,
+                              int64_t N, int64_t Np, double h, const int *__restrict__ valid) {
+    if (*valid == 0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double X[D];
+        float S[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) { X[c] = x[c * Np + i]; S[c] = f64_to_f32_fast(sconv[c * Np + i]); }
+        cubic_start<D>(X, S, h, y + i, Np);
+    }
+}
+
+cudaError_t launch_carry_start(ssm_ctx *c) {
+    int64_t blocks = (c->N + 255) / 256;
+    if (blocks > (int64_t)c->sms * 8) blocks = (int64_t)c->sms * 8;
+    if (c->d == 1)
+        k_carry_start<1><<<(unsigned)blocks, 256, 0, c->st>>>(c->x, c->y, c->sconv, c->N, c->Np, c->h, c->ws_prev);
+    else
+        k_carry_start<3><<<(unsigned)blocks, 256, 0, c->st>>>(c->x, c->y, c->sconv, c->N, c->Np, c->h, c->ws_prev);
+    return cudaGetLastError();
 }
 
 // The learned start on the form the context selects (ssm_opts.ws_forward): 0 =

@@ -578,7 +578,7 @@ __global__ void k_mi_commit(double *__restrict__ y, const double *__restrict__ p
 // else null): the particles accepted at the FP32 floor in the step's last pass.
 __global__ void k_step_stats(const int *cnt, int kmax, long long N, long long *counters, const int *mi_flags,
                              int *ws_prev) {
-    if (ws_prev) *ws_prev = 1;   // learned start: this step's predictions and converged sums match
+    if (ws_prev) *ws_prev = 1;   // learned or carried start: this step's converged sums (and predictions) match
     long long rows = 0, npass = 0;
     for (int k = 0; k < kmax; ++k) {
         rows += cnt[k];
@@ -945,7 +945,8 @@ cudaError_t launch_mi_pass(ssm_ctx *c, int pass, int fp32) {
 }
 
 cudaError_t launch_step_stats(ssm_ctx *c) {
-    const bool learned = c->prec == SSM_FP32C_LEARNED && c->ws_loaded && !c->opt.measure_y;
+    // the learned start and the carried start read the converged sums of a completed step
+    const bool learned = (c->prec == SSM_FP32C_LEARNED && c->ws_loaded && !c->opt.measure_y) || c->opt.carry_start;
     k_step_stats<<<1, 1, 0, c->st>>>(c->cnt, c->kmax, c->N, c->counters, c->opt.measure_y ? c->mif : nullptr,
                                      learned ? c->ws_prev : nullptr);
     return cudaGetLastError();

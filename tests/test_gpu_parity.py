@@ -317,6 +317,44 @@ def test_set_plan_chunks_rejects_out_of_range(S):
     s.close()
 
 
+def test_carried_start_keeps_the_roots_and_saves_a_pass(S):
+    """ssm_opts.carry_start: from the second step on, step 1 starts from the previous
+    step's converged pair sums.  The FP64 form still matches the oracle to 1e-10 per
+    particle after 12 steps; in the FP32C form every root passes the same residual
+    test as from the plain start (within K x 2 x 64 tol of the plain run after K
+    steps), with at most 80% of its pair rows."""
+    N, h, K = 640, 2.0 ** -8, 12
+    s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=15, carry_start=1)
+    s.run_steps(K)
+    x, _ = s.get_state()
+    st = s.stats()
+    s.close()
+    P = O.problem(d=3, coef=O.COEF_COUPLED3D, N=N, h=h, seed=15)
+    xo = O.run(P, O.init_x0(P), 0, K)
+    assert relerr(x, xo) < 1e-10
+    N, K = 4096, 24
+    runs = []
+    for carry in (0, 1):
+        s = S.SSM(d=3, N=N, h=h, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=16, precision=S.SSM_FP32C, carry_start=carry)
+        s.run_steps(K)
+        runs.append((s.get_state()[0], s.stats()))
+        s.close()
+    (xp, sp), (xc, sc) = runs
+    tol = max(1e-10, 2.0 ** -27 * h * (1.0 + 64.0 / math.sqrt(N)))
+    assert np.max(np.abs(xc - xp)) < K * 2 * 64 * tol
+    print("pair rows per step: plain %.0f, carried start %.0f" % (sp["newton_rows"] / K, sc["newton_rows"] / K))
+    assert sc["newton_rows"] <= 0.8 * sp["newton_rows"]
+
+
+def test_carried_start_is_rejected_where_it_does_not_apply(S):
+    for kw in (dict(coef=S.SSM_COEF_OU, d=3), dict(coef=S.SSM_COEF_CUBIC1D_GAUSS, d=1),
+               dict(coef=S.SSM_COEF_COUPLED3D, d=3, precision=S.SSM_FP32C_LEARNED),
+               dict(coef=S.SSM_COEF_COUPLED3D, d=3, measure_y=1), dict(coef=S.SSM_COEF_COUPLED3D, d=3, carry_start=2)):
+        kw.setdefault("carry_start", 1)
+        with pytest.raises(S.SSMError):
+            S.SSM(N=100, h=2.0 ** -8, T=1.0, seed=1, **kw)
+
+
 def test_set_plan_rejects_unknown_shape(S):
     s = S.SSM(d=3, N=100, h=2.0 ** -8, T=1.0, coef=S.SSM_COEF_COUPLED3D, seed=1)   # FP64: no packed kernels
     with pytest.raises(S.SSMError):
