@@ -146,7 +146,8 @@ typedef struct {
                                N not a multiple of 128, so the index lies inside the padded
                                arrays) for the bounds checks to report as SSM_EBOUNDS.  Must be 0
                                otherwise (SSM_EINVAL). */
-    int carry_start;        /* coupled sets, SSM_FP64 and SSM_FP32C, step 1 against mu^X: 0
+    int carry_start;        /* coupled sets (single contexts and batches), SSM_FP64 and
+                               SSM_FP32C, step 1 against mu^X: 0
                                (default) = step 1 starts at Y = X; 1 = from the second step of
                                a run on (and after ssm_set_state at the same step index) it
                                starts at the root of u = X + h(-u|u|^2 + S* / 2), S* the

@@ -47,12 +47,13 @@ constexpr int SEGT = 256;    // threads (and particles per segment) of the O(N) 
 constexpr int64_t NMAX_ENS = (int64_t)1 << 24;
 
 struct BEns {                // one ensemble, in device memory
-    int d, active, fine_r, chunks, fp32, pad_;
+    int d, active, fine_r, chunks, fp32, carry;   // carry: ssm_opts.carry_start
     int64_t N, Np, M, chunk_len, seg0, nseg;
     long long n;
     uint64_t seed;
     double h, sqrt_h, sqrt_hf, scale, bscale, tol;
     double *x, *y, *part, *mom;
+    double *sconv;            // converged step-1 pair sums of the last step (carry only)
     int *act0, *act1, *cnt;
     float *rprev;
 };
@@ -115,7 +116,10 @@ __device__ __forceinline__ bool last_block_of(unsigned *ticket) {
 
 // ---- phase kernels ----------------------------------------------------------
 
-// Plain start of step 1 (Y = X, every target active) for every unfinished ensemble.
+// Start of step 1 (every target active) for every unfinished ensemble: Y = X, or with
+// ssm_opts.carry_start from its second step on the carried start of the single
+// contexts (the root of u = X + h(-u|u|^2 + S*/2) with the particle's converged pair
+// sum S* of the previous step).
 __device__ __forceinline__ void plain_start(BEns *ens, int n_ens, BGlobal *g, int kmax) {
     __shared__ long long pref[MAX_ENS + 1];
     block_prefix(pref, n_ens, [&](int e) -> long long { return ens[e].active ? ens[e].N : 0; });
@@ -126,6 +130,21 @@ __device__ __forceinline__ void plain_start(BEns *ens, int n_ens, BGlobal *g, in
         const BEns &E = ens[e];
         const int64_t i = idx - pref[e];
         for (int c = 0; c < E.d; ++c) E.y[c * E.Np + i] = E.x[c * E.Np + i];
+        if (E.carry && E.n > 0) {
+            if (E.d == 1) {
+                const double X[1] = {E.x[i]};
+                const float Sc[1] = {f64_to_f32_fast(E.sconv[i])};
+                cubic_start<1>(X, Sc, E.h, E.y + i, E.Np);
+            } else {
+                double X[3];
+                float Sc[3];
+                for (int c = 0; c < 3; ++c) {
+                    X[c] = E.x[c * E.Np + i];
+                    Sc[c] = f64_to_f32_fast(E.sconv[c * E.Np + i]);
+                }
+                cubic_start<3>(X, Sc, E.h, E.y + i, E.Np);
+            }
+        }
         E.act0[i] = (int)i;
         if (i == 0) {
             E.cnt[0] = (int)E.N;
@@ -214,6 +233,9 @@ __device__ __forceinline__ int update_one(const BEns &E, int pass, int64_t t, in
     if (r == UPD_CONTINUE || r == UPD_CONVERGED || r == UPD_FLOOR)
 #pragma unroll
         for (int c = 0; c < D; ++c) E.y[c * E.Np + i] = Y[c];
+    if (E.carry && (r == UPD_CONVERGED || r == UPD_FLOOR))
+#pragma unroll
+        for (int c = 0; c < D; ++c) E.sconv[c * E.Np + i] = S[c];
     return r;
 }
 
@@ -557,6 +579,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
     if (opts) o = *opts; else ssm_opts_default(&o);
     if (o.precision != SSM_FP64 && o.precision != SSM_FP32C) return SSM_EINVAL;
     if (o.measure_y != 0) return SSM_EINVAL;   // the batched form steps the SSM (mu^X in step 1)
+    if (o.carry_start != 0 && o.carry_start != 1) return SSM_EINVAL;
     if (o.newton_kmax <= 0) o.newton_kmax = 12;
     if (o.newton_kmax > 64) return SSM_EINVAL;
     for (int e = 0; e < n; ++e) {
@@ -592,7 +615,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
     std::vector<int64_t> off(n);
     size_t o8 = 0;
     auto take = [&](size_t bytes) { size_t at = o8; o8 = (o8 + bytes + 255) & ~(size_t)255; return at; };
-    struct Offs { size_t x, y, part, mom, a0, a1, cnt, rp; };
+    struct Offs { size_t x, y, part, mom, a0, a1, cnt, rp, sc; };
     std::vector<Offs> of(n);
     long long nseg_total = 0;
     for (int k = 0; k < n; ++k) {
@@ -607,6 +630,7 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         of[k].a1 = take(sizeof(int) * Np);
         of[k].rp = take(sizeof(float) * Np);
         of[k].cnt = take(sizeof(int) * (b->kmax + 2));
+        of[k].sc = take(o.carry_start ? sizeof(double) * D.d * Np : 0);
         nseg_total += (D.N + SEGT - 1) / SEGT;
     }
     const size_t o_ens = take(sizeof(BEns) * n), o_g = take(sizeof(BGlobal)), o_seg = take(sizeof(long long) * (n + 1));
@@ -649,6 +673,8 @@ ssm_status ssm_batch_create(int n, const ssm_ens_desc *desc, const ssm_opts *opt
         E.act1 = (int *)(b->mem + of[k].a1);
         E.rprev = (float *)(b->mem + of[k].rp);
         E.cnt = (int *)(b->mem + of[k].cnt);
+        E.carry = o.carry_start;
+        E.sconv = o.carry_start ? (double *)(b->mem + of[k].sc) : nullptr;
         E.seg0 = segp[k];
         E.nseg = (D.N + SEGT - 1) / SEGT;
         segp[k + 1] = segp[k] + E.nseg;

@@ -140,6 +140,46 @@ __device__ __forceinline__ int newton_update_particle(double *S, double Sw, doub
     return UPD_CONTINUE;
 }
 
+// A start of step 1 from a pair sum S (predicted, or carried from the previous step):
+// Y^0 = X + delta with delta the root of
+// delta = h(-(X + delta)|X + delta|^2 + 0.5 S), by Newton in FP32 on delta (the
+// Jacobian a I + 2h u u^T, u = X + delta, inverted by Sherman-Morrison with one
+// reciprocal for 1/a and 1/(a + 2h|u|^2)); FP32 on the small increment is far more
+// accurate than the start needs (the prediction itself is good to ~1e-6), and the FP64
+// state keeps X exact.  A non-finite result leaves the plain start Y = X.
+template <int D>
+__device__ __forceinline__ void cubic_start(const double (&X)[D], const float (&S)[D], double h, double *yi,
+                                            int64_t Np) {
+    const float hf = (float)h;
+    float xf[D], s2[D], dl[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { xf[c] = f64_to_f32_fast(X[c]); s2[c] = 0.5f * hf * S[c]; dl[c] = 0.0f; }
+    for (int it = 0; it < 10; ++it) {
+        float u[D], g[D], uu = 0.0f, ug = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { u[c] = xf[c] + dl[c]; uu += u[c] * u[c]; }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { g[c] = dl[c] + hf * u[c] * uu - s2[c]; ug += u[c] * g[c]; }
+        const float a = 1.0f + hf * uu, b = a + 2.0f * hf * uu;
+        const float r = 1.0f / (a * b);
+        const float ia = b * r, f = 2.0f * hf * ug * (a * r);
+        float smax = 0.0f, dmax = 0.0f;
+        bool fin = true;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float st = (g[c] - f * u[c]) * ia;
+            dl[c] -= st;
+            smax = fmaxf(smax, fabsf(st));
+            dmax = fmaxf(dmax, fabsf(dl[c]));
+            fin = fin && isfinite(dl[c]);
+        }
+        if (!fin) return;   // a non-finite result leaves the plain start
+        if (smax <= 1e-7f * dmax) break;
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) yi[c * Np] = X[c] + f32_to_f64(dl[c]);
+}
+
 // Brownian increment dW_n^i on the step's own grid (fine_r <= 1) or as the sum of
 // fine_r increments of the finer grid (runs at different h share one path).
 template <int D>

@@ -77,6 +77,36 @@ def test_batch_matches_single_contexts(S, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_batch_carried_start_matches_single_contexts(S, prec):
+    """ssm_opts.carry_start in the batched form: every ensemble ends where a single
+    context of it with the carried start ends (same tolerances as from the plain
+    start), with fewer step-1 pair rows than the batch from the plain start."""
+    rows = []
+    for carry in (0, 1):
+        b = S.Batch(MIXED, precision=prec, carry_start=carry)
+        b.run()
+        b.sync()
+        if carry:
+            for e, dsc in enumerate(MIXED):
+                xb, nb = b.get_state(e)
+                s = S.SSM(d=dsc["d"], N=dsc["N"], h=dsc["h"], T=dsc["T"], coef=_coef(S, dsc["d"]),
+                          seed=dsc["seed"], precision=prec, carry_start=1)
+                s.run()
+                xs, ns = s.get_state()
+                s.close()
+                assert nb == ns
+                if prec == 0:
+                    assert relerr(xb, xs) < 1e-11, e
+                else:
+                    assert np.max(np.abs(xb - xs)) < 1e-7, e
+        rows.append(b.stats()["newton_rows"])
+        b.close()
+    # these ensembles take 4 to 32 steps of h = 2^-3 .. 2^-6 (the first step of each
+    # starts plain): about 14% fewer rows here, a third fewer at the benchmark's h
+    assert rows[1] < 0.9 * rows[0], rows
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_batch_matches_oracle(S, prec):
     descs = [dict(d=1, N=333, h=2.0 ** -5, T=1.0, seed=7), dict(d=3, N=257, h=2.0 ** -4, T=1.0, seed=8)]
     b = S.Batch(descs, precision=prec)
